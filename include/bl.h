@@ -1,0 +1,257 @@
+/*
+ * bl.h -- C ABI of the GB300 beamline tracking library (libbl.so).
+ *
+ * The library tracks a 6D electron bunch, in coordinates relative to a
+ * reference particle, through a beamline of linear transport elements and
+ * plasma accelerator stages. Each element is a per-particle transfer map
+ * f: R^6 -> R^6 (paper Sec. 1, valid without collective effects). A plasma
+ * stage is either a classical RK4 push through a prescribed linear wake or a
+ * learned MLP surrogate of that push (Sec. 3, Sec. 4.3). Particle arrays live
+ * on the device and are owned by the caller; every call updates them in
+ * place, as the paper's zero-copy views let the ML framework and the tracking
+ * code share device memory (Sec. 2).
+ *
+ * Coordinates (all six arrays of one bunch have the same dtype and length n):
+ *   x, y  [m]                transverse offsets
+ *   px, py                   p_x / p_ref, p_y / p_ref
+ *   t     [m]                c * (arrival-time offset), t = zeta_ref - zeta
+ *   pt                       -(gamma - gamma_ref) / (beta gamma)_ref
+ *
+ * Conventions for every call:
+ *   - Returns a bl_status; BL_OK on success. No exception crosses the ABI.
+ *     bl_last_error_message() returns a per-thread description of the last
+ *     failure.
+ *   - Work is enqueued on the given CUDA stream (NULL = legacy default
+ *     stream). Outputs that the call states are "host" are written before the
+ *     call returns (the call synchronises the stream); all other outputs are
+ *     valid after the stream is synchronised.
+ *   - Pointers documented as "device" must be device (or managed) memory of
+ *     the current device; "host" pointers are ordinary host memory.
+ *   - Arguments are checked on the host before any work is enqueued; an
+ *     invalid argument returns BL_ERR_INVALID_ARG and enqueues nothing.
+ *   - The library keeps a scratch workspace per (device, stream). Calls on the
+ *     same stream are ordered; calls on different streams use different
+ *     workspaces and may run concurrently if they touch different particles.
+ *   - Kernels that wait on the tensor core give up after a bounded spin and
+ *     raise a device flag; bl_poll_device_errors() reports it as
+ *     BL_ERR_TIMEOUT.
+ */
+#ifndef BL_H
+#define BL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *bl_stream; /* same type as cudaStream_t */
+
+typedef enum {
+  BL_OK = 0,
+  BL_ERR_INVALID_ARG = 1,
+  BL_ERR_CUDA = 2,
+  BL_ERR_OOM = 3,
+  BL_ERR_UNSUPPORTED_ARCH = 4,
+  BL_ERR_NONFINITE = 5,
+  BL_ERR_TIMEOUT = 6,
+  BL_ERR_STATE = 7
+} bl_status;
+
+typedef enum { BL_F32 = 0, BL_F64 = 1 } bl_dtype;
+
+/* Objectives of bl_track_grad (final beam quantities, Sec. 4 moments). */
+typedef enum {
+  BL_OBJ_EPS_N_X = 0, /* normalised emittance, x plane */
+  BL_OBJ_SIGMA_X = 1, /* rms beam size, x plane */
+  BL_OBJ_EPS_N_Y = 2,
+  BL_OBJ_SIGMA_Y = 3
+} bl_objective;
+
+/* A bunch, or a batch of independent bunches stored back to back.
+ * Particle arrays: device, dtype `dtype`, n elements each, caller-owned.
+ * Bunch b occupies particles [offsets[b], offsets[b+1]); offsets has
+ * n_bunch+1 entries with offsets[0] = 0 and offsets[n_bunch] = n. When
+ * n_bunch == 1 both offset pointers may be NULL. offsets_dev is device
+ * memory and offsets_host the same values in host memory (the host copy lets
+ * the library plan its grids without a device round trip).
+ * gamma_ref is the reference particle's Lorentz factor (host value, shared by
+ * all bunches); bl_track advances it through every plasma stage. */
+typedef struct {
+  void *x, *px, *y, *py, *t, *pt;
+  int64_t n;
+  int32_t n_bunch;
+  int32_t dtype;
+  const int64_t *offsets_dev;
+  const int64_t *offsets_host;
+  double gamma_ref;
+} bl_bunch;
+
+typedef enum { BL_DRIFT = 0, BL_QUAD = 1, BL_SBEND = 2, BL_PLASMA = 3 } bl_kind;
+
+struct bl_surrogate_s;
+typedef struct bl_surrogate_s bl_surrogate;
+struct bl_lattice_s;
+typedef struct bl_lattice_s bl_lattice;
+
+/* One beamline element.
+ *   BL_DRIFT:  L [m]
+ *   BL_QUAD:   L [m], k [1/m^2] (k > 0 focuses x); per_bunch_k: host array of
+ *              n_bunch_k strengths that override k bunch by bunch, or NULL
+ *   BL_SBEND:  L [m] arc length, angle [rad] (sector bend, no edge focusing)
+ *   BL_PLASMA: L [m], nsteps RK4 steps, n0_cm3 plasma density [1/cm^3],
+ *              E0_Vpm wake amplitude [V/m], phi0 reference phase [rad];
+ *              surrogate: trained stage surrogate, or NULL for the RK4 push.
+ * The linear maps are the solutions of the linear equations of motion of
+ * H = px^2/2 + py^2/2 + pt^2/(2 b^2 g^2) + h^2 x^2/2 + h x pt/b + k (x^2-y^2)/2
+ * (h = angle/L in a bend); the paper (Sec. 1, Sec. 4) treats them as given
+ * conventional elements. */
+typedef struct {
+  int32_t kind;
+  int32_t nsteps;
+  double L, k, angle;
+  double n0_cm3, E0_Vpm, phi0;
+  const bl_surrogate *surrogate;
+  const double *per_bunch_k;
+} bl_element;
+
+/* Compile a beamline. elements: host array of n_elements entries (copied).
+ * n_bunch_k: length of every non-NULL per_bunch_k array (0 if none).
+ * Consecutive linear elements are fused into one segment map per bunch. The
+ * lattice keeps pointers to the surrogates it names: they must outlive it. */
+bl_status bl_lattice_create(const bl_element *elements, int32_t n_elements,
+                            int32_t n_bunch_k, bl_lattice **out);
+bl_status bl_lattice_destroy(bl_lattice *lat);
+int32_t bl_lattice_num_elements(const bl_lattice *lat);
+int32_t bl_lattice_num_quads(const bl_lattice *lat);
+
+/* Track the bunch through the lattice (Sec. 2/4.3: conventional elements and
+ * plasma stages in one s-based loop, particles never leaving the device).
+ * moments_out: host, n_elements * n_bunch * 28 doubles, or NULL. Entry
+ * [e][b] holds the moments of bunch b after element e as
+ * [N, 6 means, 21 central second moments S_ab, a <= b, row-major over
+ * (x, px, y, py, t, pt)] with normalisation 1/N (Sec. 4 moments). Linear
+ * elements' moments are propagated in FP64 (mu <- M mu, S <- M S M^T) from a
+ * reduction at each segment's entry. When moments_out is non-NULL the call
+ * synchronises the stream. nonfinite_out: host, or NULL; receives the number
+ * of non-finite coordinates seen by the moment reductions (the particles are
+ * kept). bunch->gamma_ref is advanced to the reference energy at the exit. */
+bl_status bl_track(bl_bunch *bunch, const bl_lattice *lat, double *moments_out,
+                   int64_t *nonfinite_out, bl_stream stream);
+
+/* Per-bunch moments of the current particles (Sec. 4 moments, definitions as
+ * in bl_track). out: host or device, n_bunch * 28 doubles; valid after the
+ * stream is synchronised. Accumulation: exact FP32 products and float-float
+ * sums per thread, FP64 across threads. Uses library scratch memory. */
+bl_status bl_moments(const bl_bunch *bunch, double *out, bl_stream stream);
+
+/* Apply one 6x6 matrix (host, row-major, 36 doubles, or n_bunch*36 for one
+ * matrix per bunch when per_bunch != 0) to every particle: z <- M z. */
+bl_status bl_apply_linear(bl_bunch *bunch, const double *M, int32_t per_bunch,
+                          bl_stream stream);
+
+/* Push every particle through one prescribed-wake plasma stage with classical
+ * RK4 (the plain method a surrogate replaces, Sec. 4). The stage is given by
+ * an element of kind BL_PLASMA (its surrogate field is ignored).
+ * bunch->gamma_ref is advanced to the reference energy at the exit (FP64
+ * reference particle on the host). FP32 bunches are integrated in
+ * a deviation form relative to the FP64 reference trajectory; FP64 bunches in
+ * FP64. */
+bl_status bl_push_stage(bl_bunch *bunch, const bl_element *stage, bl_stream stream);
+
+/* FP64 on-axis reference particle through one stage (host computation).
+ * Returns gamma at the exit given gamma at the entry. */
+bl_status bl_reference_exit(const bl_element *stage, double gamma_in,
+                            double *gamma_out);
+
+/* ---------------------------------------------------------------- MLP ---- */
+
+/* Surrogate network F = L4 o s o L3 o s o L2 o s o L1 o s o L0 (Sec. 3, Eq.
+ * for F) with widths 6 -> 128 -> 128 -> 128 -> 128 -> 6 and s = GELU
+ * (tanh form). Weights W[l] are (out x in) row-major FP32 masters; the
+ * device computes with BF16 copies and FP32 accumulation. mu/sd: FP64
+ * per-coordinate normalisation of inputs and outputs (Sec. 3 data
+ * preparation). All pointers are host memory and are copied. */
+typedef struct {
+  int32_t n_layers;          /* must be 5 */
+  const int32_t *widths;     /* n_layers + 1 entries: 6,128,128,128,128,6 */
+  const float *const *W;     /* n_layers pointers */
+  const float *const *b;     /* n_layers pointers */
+  const double *mu_in, *sd_in, *mu_out, *sd_out; /* 6 each */
+} bl_mlp_desc;
+
+bl_status bl_surrogate_create(const bl_mlp_desc *desc, bl_surrogate **out);
+bl_status bl_surrogate_destroy(bl_surrogate *s);
+
+/* Read back the FP32 master parameters (after synchronising the device):
+ * W_out[l] and b_out[l] are host buffers sized like the descriptor's. */
+bl_status bl_surrogate_get_params(const bl_surrogate *s, float *const *W_out,
+                                  float *const *b_out);
+
+/* Replace relative coordinates at the stage entry by the surrogate's
+ * prediction at the stage exit (Sec. 4.3 in-situ inference): FP64 normalise,
+ * tcgen05 BF16 MLP with FP32 accumulation, FP64 de-normalise. FP32 bunches
+ * only. Does not change bunch->gamma_ref. */
+bl_status bl_surrogate_apply(const bl_surrogate *s, bl_bunch *bunch, bl_stream stream);
+
+typedef struct {
+  double lr, beta1, beta2, eps;
+} bl_adam_cfg;
+
+/* One Adam step (Sec. 3: MSE loss, Adam, minibatches) on a minibatch of
+ * (input, target) pairs. in, out: device FP32, coordinate-major [6][ld];
+ * idx: device int64 array of `batch` column indices, or NULL for columns
+ * 0..batch-1. Inputs and targets are normalised with the surrogate's FP64
+ * constants; the loss is the MSE over the normalised targets.
+ * loss_out: device float, or NULL; receives the minibatch loss before the
+ * update. The step counter t used for bias correction is kept in the
+ * surrogate and advanced by one. */
+bl_status bl_surrogate_train_step(bl_surrogate *s, const float *in, const float *out,
+                                  int64_t ld, const int64_t *idx, int64_t batch,
+                                  const bl_adam_cfg *cfg, float *loss_out,
+                                  bl_stream stream);
+
+/* Gradient of the minibatch MSE (same data layout as bl_surrogate_train_step)
+ * without an update, for optimisers or data-parallel reductions outside the
+ * library. grad_out: device, BL_MLP_NPARAM floats in the flat layout
+ * [W0 (128x6), b0 (128), W1 (128x128), b1, W2, b2, W3, b3, W4 (6x128), b4 (6)],
+ * weights row-major (out x in). loss_out: device float, or NULL. */
+#define BL_MLP_NPARAM 51206
+bl_status bl_surrogate_grad(const bl_surrogate *s, const float *in, const float *out,
+                            int64_t ld, const int64_t *idx, int64_t batch, float *grad_out,
+                            float *loss_out, bl_stream stream);
+
+/* MSE of the surrogate on `count` pairs (test loss of the 70/30 split, Sec. 3)
+ * with the same layout as bl_surrogate_train_step. loss_out: device double. */
+bl_status bl_surrogate_loss(const bl_surrogate *s, const float *in, const float *out,
+                            int64_t ld, const int64_t *idx, int64_t count,
+                            double *loss_out, bl_stream stream);
+
+/* ------------------------------------------------------------ adjoint ---- */
+
+/* Objective J of the final beam (Sec. 4.4: lens strengths tuned against final
+ * beam quality) and its gradient with respect to every quadrupole strength of
+ * the lattice, in element order, by reverse mode: segment maps transposed,
+ * surrogate stages through the MLP's vector-Jacobian product recomputed from
+ * stage-entry checkpoints. Plasma stages must be surrogates. The bunch is
+ * tracked to the exit (its arrays and gamma_ref are updated as by bl_track).
+ * J_out, dJ_dk: host (n_bunch and n_bunch * n_quads doubles, bunch-major).
+ * The call synchronises the stream. */
+bl_status bl_track_grad(bl_bunch *bunch, const bl_lattice *lat, int32_t objective,
+                        double *J_out, double *dJ_dk, bl_stream stream);
+
+/* -------------------------------------------------------------- misc ---- */
+
+const char *bl_last_error_message(void);
+const char *bl_version(void);
+
+/* Read and clear the device-side error flags of the current device (bounded
+ * waits that gave up). Synchronises the device. */
+bl_status bl_poll_device_errors(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BL_H */

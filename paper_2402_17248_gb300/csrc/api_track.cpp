@@ -1,0 +1,348 @@
+// C ABI: lattices, tracking, moments, linear maps and the plain stage push.
+#include <cmath>
+
+#include "runtime.h"
+
+using namespace bl;
+
+namespace {
+
+bool lattice_has_per_bunch(const bl_lattice_s *L) { return L->n_bunch_k > 0; }
+
+double element_k(const bl_lattice_s *L, int e, int b) {
+  const auto &v = L->pbk[e];
+  return v.empty() ? L->els[e].k : v[b];
+}
+
+}  // namespace
+
+// Host plan (stage tables, segment and element matrices) for a reference
+// energy, dtype and bunch count; uploaded to device buffers owned by the lattice.
+bl_status bl::build_plan(bl_lattice_s *L, double gamma_in, int dtype, int n_bunch, cudaStream_t st) {
+  int dev = -1;
+  BL_CUDA(cudaGetDevice(&dev));
+  auto &P = L->plan;
+  if (P.valid && P.gamma_in == gamma_in && P.dtype == dtype && P.n_bunch == n_bunch &&
+      P.device == dev)
+    return BL_OK;
+  const int nbm = lattice_has_per_bunch(L) ? n_bunch : 1;
+  const size_t G = L->groups.size();
+  std::vector<StageTrack> stages(G);
+  std::vector<std::vector<Mat6>> seg(G);
+  std::vector<std::vector<std::vector<Mat6>>> elm(G);
+  std::vector<size_t> toff(G, 0), moff(G, 0);
+  size_t tbytes = 0, mbytes = 0;
+  const size_t esz = dtype == BL_F32 ? 4 : 8;
+  double gam = gamma_in;
+  for (size_t g = 0; g < G; ++g) {
+    const auto &gr = L->groups[g];
+    if (gr.stage) {
+      BL_TRY(stage_track(L->els[gr.first], gam, dtype, &stages[g]));
+      gam = stages[g].c.gamma_out;
+      toff[g] = tbytes;
+      tbytes += (size_t)stages[g].c.nsteps * 16 * esz;
+    } else {
+      const double bg = std::sqrt(gam * gam - 1.0);
+      seg[g].assign(nbm, mat_identity());
+      elm[g].resize(gr.last - gr.first + 1);
+      for (int e = gr.first; e <= gr.last; ++e) {
+        auto &em = elm[g][e - gr.first];
+        em.resize(nbm);
+        for (int b = 0; b < nbm; ++b) {
+          em[b] = element_matrix(L->els[e], element_k(L, e, b), bg);
+          seg[g][b] = mat_mul(em[b], seg[g][b]);
+        }
+      }
+      moff[g] = mbytes;
+      mbytes += (size_t)nbm * 36 * esz;
+    }
+  }
+  // device upload
+  if (P.d_tables && P.tables_bytes < tbytes) { BL_CUDA(cudaStreamSynchronize(st)); cudaFree(P.d_tables); P.d_tables = nullptr; P.tables_bytes = 0; }
+  if (P.d_mats && P.mats_bytes < mbytes) { BL_CUDA(cudaStreamSynchronize(st)); cudaFree(P.d_mats); P.d_mats = nullptr; P.mats_bytes = 0; }
+  if (!P.d_tables && tbytes) { BL_CUDA(cudaMalloc(&P.d_tables, tbytes)); P.tables_bytes = tbytes; }
+  if (!P.d_mats && mbytes) { BL_CUDA(cudaMalloc(&P.d_mats, mbytes)); P.mats_bytes = mbytes; }
+  std::vector<uint8_t> hbuf(std::max(tbytes, mbytes));
+  if (tbytes) {
+    for (size_t g = 0; g < G; ++g)
+      if (L->groups[g].stage) {
+        const void *src = dtype == BL_F32 ? (const void *)stages[g].table32.data()
+                                          : (const void *)stages[g].table64.data();
+        std::memcpy(hbuf.data() + toff[g], src, (size_t)stages[g].c.nsteps * 16 * esz);
+      }
+    BL_CUDA(cudaMemcpyAsync(P.d_tables, hbuf.data(), tbytes, cudaMemcpyHostToDevice, st));
+    BL_CUDA(cudaStreamSynchronize(st));
+  }
+  if (mbytes) {
+    for (size_t g = 0; g < G; ++g)
+      if (!L->groups[g].stage)
+        for (int b = 0; b < nbm; ++b)
+          for (int i = 0; i < 36; ++i) {
+            uint8_t *dst = hbuf.data() + moff[g] + ((size_t)b * 36 + i) * esz;
+            if (dtype == BL_F32) { float v = (float)seg[g][b][i]; std::memcpy(dst, &v, 4); }
+            else std::memcpy(dst, &seg[g][b][i], 8);
+          }
+    BL_CUDA(cudaMemcpyAsync(P.d_mats, hbuf.data(), mbytes, cudaMemcpyHostToDevice, st));
+    BL_CUDA(cudaStreamSynchronize(st));
+  }
+  P.stages = std::move(stages);
+  P.seg_mats = std::move(seg);
+  P.el_mats = std::move(elm);
+  P.table_off = std::move(toff);
+  P.mat_off = std::move(moff);
+  P.gamma_in = gamma_in;
+  P.gamma_out = gam;
+  P.dtype = dtype;
+  P.n_bunch = n_bunch;
+  P.device = dev;
+  P.valid = true;
+  return BL_OK;
+}
+
+namespace {
+
+template <typename T>
+bl_status run_segment(bl_bunch *b, bl_lattice_s *L, size_t g, bool moments, double *mom_dev,
+                      cudaStream_t st) {
+  auto &P = L->plan;
+  Soa<T> z = soa_of<T>(b);
+  const int64_t *off = b->n_bunch > 1 ? b->offsets_dev : nullptr;
+  const T *mats = (const T *)((const uint8_t *)P.d_mats + P.mat_off[g]);
+  const int per_bunch = lattice_has_per_bunch(L) ? 1 : 0;
+  void *part = nullptr;
+  if (moments)
+    BL_TRY(ws_get(st, WS_PARTIALS, (size_t)stream_slots(b->n, b->n_bunch) * 28 * sizeof(double), &part));
+  BL_CUDA(launch_stream<T>(z, z, b->n, off, b->n_bunch, mats, per_bunch, nullptr, true, moments,
+                           (double *)part, st));
+  if (moments) {
+    void *nf = nullptr;
+    BL_TRY(ws_get(st, WS_NONFINITE, sizeof(unsigned long long), &nf));
+    BL_CUDA(launch_moments_finalize((const double *)part, off, b->n_bunch, b->n, mom_dev,
+                                    (unsigned long long *)nf, st));
+  }
+  return BL_OK;
+}
+
+bl_status run_stage(bl_bunch *b, bl_lattice_s *L, size_t g, cudaStream_t st) {
+  auto &P = L->plan;
+  const bl_element &e = L->els[L->groups[g].first];
+  const StageTrack &tr = P.stages[g];
+  if (e.surrogate) {
+    BL_TRY(bl_surrogate_apply(e.surrogate, b, st));
+  } else if (b->dtype == BL_F32) {
+    const float *tab = (const float *)((const uint8_t *)P.d_tables + P.table_off[g]);
+    BL_CUDA(launch_pusher<float>(soa_of<float>(b), b->n, tr.c, tab, st));
+  } else {
+    const double *tab = (const double *)((const uint8_t *)P.d_tables + P.table_off[g]);
+    BL_CUDA(launch_pusher<double>(soa_of<double>(b), b->n, tr.c, tab, st));
+  }
+  return BL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+bl_status bl_lattice_create(const bl_element *elements, int32_t n_elements, int32_t n_bunch_k,
+                            bl_lattice **out) {
+  BL_CHECK(out, "out is NULL");
+  *out = nullptr;
+  BL_CHECK(elements && n_elements > 0, "lattice needs at least one element");
+  BL_CHECK(n_bunch_k >= 0, "n_bunch_k must be >= 0");
+  auto L = std::make_unique<bl_lattice_s>();
+  L->n_bunch_k = 0;
+  for (int i = 0; i < n_elements; ++i) {
+    const bl_element &e = elements[i];
+    BL_CHECK(e.kind >= BL_DRIFT && e.kind <= BL_PLASMA, "unknown element kind");
+    BL_CHECK(std::isfinite(e.L) && e.L >= 0.0, "element length must be finite and >= 0");
+    if (e.kind == BL_QUAD) BL_CHECK(std::isfinite(e.k), "quad strength must be finite");
+    if (e.kind == BL_SBEND) {
+      BL_CHECK(std::isfinite(e.angle), "bend angle must be finite");
+      BL_CHECK(e.angle == 0.0 || e.L > 0.0, "a bend with an angle needs L > 0");
+    }
+    if (e.kind == BL_PLASMA) {
+      BL_CHECK(e.L > 0.0, "plasma stage needs L > 0");
+      BL_CHECK(e.nsteps >= 1 && e.nsteps <= (1 << 20), "plasma stage needs 1 <= nsteps <= 2^20");
+      BL_CHECK(e.n0_cm3 > 0.0 && std::isfinite(e.E0_Vpm) && std::isfinite(e.phi0),
+               "plasma stage parameters invalid");
+    }
+    std::vector<double> pk;
+    if (e.kind == BL_QUAD && e.per_bunch_k) {
+      BL_CHECK(n_bunch_k > 0, "per_bunch_k given but n_bunch_k == 0");
+      pk.assign(e.per_bunch_k, e.per_bunch_k + n_bunch_k);
+      for (double v : pk) BL_CHECK(std::isfinite(v), "per_bunch_k must be finite");
+      L->n_bunch_k = n_bunch_k;
+    }
+    L->els.push_back(e);
+    L->pbk.push_back(std::move(pk));
+    if (e.kind == BL_QUAD) L->n_quads++;
+  }
+  for (int i = 0; i < n_elements; ++i) {
+    const bool st = L->els[i].kind == BL_PLASMA;
+    if (st || L->groups.empty() || L->groups.back().stage)
+      L->groups.push_back({st, i, i});
+    else
+      L->groups.back().last = i;
+  }
+  *out = L.release();
+  return BL_OK;
+}
+
+bl_status bl_lattice_destroy(bl_lattice *lat) {
+  delete lat;
+  return BL_OK;
+}
+
+int32_t bl_lattice_num_elements(const bl_lattice *lat) { return lat ? (int32_t)lat->els.size() : -1; }
+int32_t bl_lattice_num_quads(const bl_lattice *lat) { return lat ? lat->n_quads : -1; }
+
+bl_status bl_track(bl_bunch *b, const bl_lattice *lat_c, double *moments_out,
+                   int64_t *nonfinite_out, bl_stream stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  std::string why;
+  BL_CHECK(lat_c, "lattice is NULL");
+  BL_CHECK(bunch_dims_ok(b, &why), why);
+  bl_lattice_s *L = const_cast<bl_lattice_s *>(lat_c);
+  BL_CHECK(!lattice_has_per_bunch(L) || L->n_bunch_k == b->n_bunch,
+           "lattice per-bunch strengths do not match the bunch count");
+  for (const auto &gr : L->groups)
+    if (gr.stage && L->els[gr.first].surrogate)
+      BL_CHECK(b->dtype == BL_F32, "surrogate stages need an FP32 bunch");
+  DevCtx *ctx = nullptr;
+  BL_TRY(current_ctx(&ctx));
+  std::lock_guard<std::mutex> lk(L->mu);
+  BL_TRY(build_plan(L, b->gamma_ref, b->dtype, b->n_bunch, st));
+  const auto &P = L->plan;
+  const bool want = moments_out != nullptr || nonfinite_out != nullptr;
+  const size_t G = L->groups.size();
+  // reduction points: segment entries, and stage exits not followed by a segment
+  std::vector<int> red_of(G, -1);
+  int R = 0;
+  for (size_t g = 0; g < G; ++g) {
+    if (!L->groups[g].stage) red_of[g] = R++;
+    else if (g + 1 == G || L->groups[g + 1].stage) red_of[g] = R++;
+  }
+  double *mom_dev = nullptr;
+  void *nf = nullptr;
+  const size_t per = (size_t)b->n_bunch * 28;
+  if (want) {
+    void *p = nullptr;
+    BL_TRY(ws_get(st, WS_MOMENTS, (size_t)R * per * sizeof(double), &p));
+    mom_dev = (double *)p;
+    BL_TRY(ws_get(st, WS_NONFINITE, sizeof(unsigned long long), &nf));
+    BL_CUDA(cudaMemsetAsync(nf, 0, sizeof(unsigned long long), st));
+  }
+  for (size_t g = 0; g < G; ++g) {
+    if (L->groups[g].stage) {
+      BL_TRY(run_stage(b, L, g, st));
+      if (want && red_of[g] >= 0)
+        BL_TRY(moments_device(b, mom_dev + red_of[g] * per, (unsigned long long *)nf, st));
+    } else if (b->dtype == BL_F32) {
+      BL_TRY(run_segment<float>(b, L, g, want, want ? mom_dev + red_of[g] * per : nullptr, st));
+    } else {
+      BL_TRY(run_segment<double>(b, L, g, want, want ? mom_dev + red_of[g] * per : nullptr, st));
+    }
+  }
+  b->gamma_ref = P.gamma_out;
+  if (!want) return BL_OK;
+  std::vector<double> red((size_t)R * per);
+  unsigned long long nonfin = 0;
+  BL_CUDA(cudaMemcpyAsync(red.data(), mom_dev, red.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  BL_CUDA(cudaMemcpyAsync(&nonfin, nf, sizeof(nonfin), cudaMemcpyDeviceToHost, st));
+  BL_CUDA(cudaStreamSynchronize(st));
+  if (nonfinite_out) *nonfinite_out = (int64_t)nonfin;
+  if (moments_out) {
+    const int nbm = lattice_has_per_bunch(L) ? b->n_bunch : 1;
+    for (size_t g = 0; g < G; ++g) {
+      const auto &gr = L->groups[g];
+      if (gr.stage) {
+        const int r = red_of[g] >= 0 ? red_of[g] : red_of[g + 1];
+        std::memcpy(moments_out + (size_t)gr.first * per, red.data() + (size_t)r * per,
+                    per * sizeof(double));
+      } else {
+        for (int bb = 0; bb < b->n_bunch; ++bb) {
+          double cur[28];
+          std::memcpy(cur, red.data() + (size_t)red_of[g] * per + (size_t)bb * 28, sizeof(cur));
+          for (int e = gr.first; e <= gr.last; ++e) {
+            double nxt[28];
+            propagate_moments(P.el_mats[g][e - gr.first][nbm > 1 ? bb : 0], cur, nxt);
+            std::memcpy(moments_out + (size_t)e * per + (size_t)bb * 28, nxt, sizeof(nxt));
+            std::memcpy(cur, nxt, sizeof(cur));
+          }
+        }
+      }
+    }
+  }
+  if (nonfin) return set_error(BL_ERR_NONFINITE, std::to_string(nonfin) + " non-finite particles seen");
+  return BL_OK;
+}
+
+bl_status bl_moments(const bl_bunch *b, double *out, bl_stream stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  std::string why;
+  BL_CHECK(bunch_dims_ok(b, &why), why);
+  BL_CHECK(out, "out is NULL");
+  DevCtx *ctx = nullptr;
+  BL_TRY(current_ctx(&ctx));
+  void *p = nullptr;
+  BL_TRY(ws_get(st, WS_MOMENTS, (size_t)b->n_bunch * 28 * sizeof(double), &p));
+  BL_TRY(moments_device(b, (double *)p, nullptr, st));
+  BL_CUDA(cudaMemcpyAsync(out, p, (size_t)b->n_bunch * 28 * sizeof(double), cudaMemcpyDefault, st));
+  return BL_OK;
+}
+
+bl_status bl_apply_linear(bl_bunch *b, const double *M, int32_t per_bunch, bl_stream stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  std::string why;
+  BL_CHECK(bunch_dims_ok(b, &why), why);
+  BL_CHECK(M, "matrix is NULL");
+  DevCtx *ctx = nullptr;
+  BL_TRY(current_ctx(&ctx));
+  const int nm = per_bunch ? b->n_bunch : 1;
+  for (int i = 0; i < nm * 36; ++i) BL_CHECK(std::isfinite(M[i]), "matrix entries must be finite");
+  const size_t esz = b->dtype == BL_F32 ? 4 : 8;
+  void *d = nullptr;
+  BL_TRY(ws_get(st, WS_MATS, (size_t)nm * 36 * esz, &d));
+  std::vector<uint8_t> h((size_t)nm * 36 * esz);
+  for (int i = 0; i < nm * 36; ++i) {
+    if (esz == 4) { float v = (float)M[i]; std::memcpy(&h[i * 4], &v, 4); }
+    else std::memcpy(&h[i * 8], &M[i], 8);
+  }
+  // a pageable-source copy has consumed the host buffer when it returns
+  BL_CUDA(cudaMemcpyAsync(d, h.data(), h.size(), cudaMemcpyHostToDevice, st));
+  const int64_t *off = b->n_bunch > 1 ? b->offsets_dev : nullptr;
+  if (b->dtype == BL_F32) {
+    Soa<float> z = soa_of<float>(b);
+    BL_CUDA(launch_stream<float>(z, z, b->n, off, b->n_bunch, (const float *)d, per_bunch ? 1 : 0,
+                                 nullptr, true, false, nullptr, st));
+  } else {
+    Soa<double> z = soa_of<double>(b);
+    BL_CUDA(launch_stream<double>(z, z, b->n, off, b->n_bunch, (const double *)d, per_bunch ? 1 : 0,
+                                  nullptr, true, false, nullptr, st));
+  }
+  return BL_OK;
+}
+
+bl_status bl_push_stage(bl_bunch *b, const bl_element *stage, bl_stream stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  std::string why;
+  BL_CHECK(bunch_dims_ok(b, &why), why);
+  BL_CHECK(stage && stage->kind == BL_PLASMA, "stage must be a BL_PLASMA element");
+  DevCtx *ctx = nullptr;
+  BL_TRY(current_ctx(&ctx));
+  StageTrack tr;
+  BL_TRY(stage_track(*stage, b->gamma_ref, b->dtype, &tr));
+  const size_t bytes = (size_t)tr.c.nsteps * 16 * (b->dtype == BL_F32 ? 4 : 8);
+  void *d = nullptr;
+  BL_TRY(ws_get(st, WS_TABLES, bytes, &d));
+  const void *src = b->dtype == BL_F32 ? (const void *)tr.table32.data() : (const void *)tr.table64.data();
+  BL_CUDA(cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, st));
+  if (b->dtype == BL_F32)
+    BL_CUDA(launch_pusher<float>(soa_of<float>(b), b->n, tr.c, (const float *)d, st));
+  else
+    BL_CUDA(launch_pusher<double>(soa_of<double>(b), b->n, tr.c, (const double *)d, st));
+  b->gamma_ref = tr.c.gamma_out;
+  return BL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,109 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+#include <cuda_runtime.h>
+
+#include "../../include/bl.h"
+
+namespace bl {
+
+template <typename T> struct Soa { T *c[6]; };
+
+// Particles per block of the streaming kernels and its thread count.
+constexpr int STREAM_THREADS = 256;
+constexpr int64_t STREAM_CHUNK = 4096;
+
+inline int64_t stream_blocks(int64_t n) { return (n + STREAM_CHUNK - 1) / STREAM_CHUNK; }
+// Partial-sum slots of a segmented reduction: slot (bunch + block) is unique
+// because bunches and blocks both tile the particle range contiguously.
+inline int64_t stream_slots(int64_t n, int n_bunch) { return stream_blocks(n) + n_bunch; }
+
+// ---- streaming kernels (linear.cu) ----
+// z_out = M_b (z_in - c_b) for particles of bunch b (c_b = 0 when c == NULL),
+// optionally reducing moments of z_in into `partials` (28 doubles per slot).
+template <typename T>
+cudaError_t launch_stream(Soa<T> zin, Soa<T> zout, int64_t n, const int64_t *offsets,
+                          int n_bunch, const T *mats, int per_bunch, const T *centers,
+                          bool apply, bool moments, double *partials, cudaStream_t st);
+cudaError_t launch_moments_finalize(const double *partials, const int64_t *offsets,
+                                    int n_bunch, int64_t n, double *out,
+                                    unsigned long long *nonfinite, cudaStream_t st);
+// lambda <- M_b^T lambda and cross[b] += sum_i lambda_out,i z_in,i^T (36 per slot).
+template <typename T>
+cudaError_t launch_linear_adjoint(Soa<T> lam, Soa<T> zin, int64_t n, const int64_t *offsets,
+                                  int n_bunch, const T *mats, int per_bunch,
+                                  double *partials, cudaStream_t st);
+cudaError_t launch_cross_finalize(const double *partials, const int64_t *offsets,
+                                  int n_bunch, int64_t n, double *out, cudaStream_t st);
+
+// ---- plasma stage pusher (pusher.cu) ----
+struct StageConsts {
+  double kp, g, K0, h;
+  double bg_in, gamma_in, bg_out, gamma_out;
+  double uz_ref_out;
+  int nsteps;
+};
+// table: nsteps*4 entries of 4 values (T), see pusher.cu for the layout.
+template <typename T>
+cudaError_t launch_pusher(Soa<T> z, int64_t n, const StageConsts &c, const T *table,
+                          cudaStream_t st);
+
+// ---- MLP (mlp_fwd.cu, mlp_train.cu) ----
+constexpr int MLP_H = 128;
+constexpr int MLP_NPARAM = 128 * 6 + 128 + 3 * (128 * 128 + 128) + 6 * 128 + 6;  // 51206
+// Offsets of W[l] and b[l] in the flat FP32 parameter vector.
+inline int mlp_w_off(int l) {
+  static const int o[5] = {0, 896, 17408, 33920, 50432};
+  return o[l];
+}
+inline int mlp_b_off(int l) {
+  static const int o[5] = {768, 17280, 33792, 50304, 51200};
+  return o[l];
+}
+// Size in bytes of the BF16 UMMA weight image and its FP32 bias block.
+constexpr int MLP_IMG_W0 = 128 * 16 * 2;
+constexpr int MLP_IMG_WH = 128 * 128 * 2;
+constexpr int MLP_IMG_W4 = 16 * 128 * 2;
+constexpr int MLP_IMG_BYTES = MLP_IMG_W0 + 3 * MLP_IMG_WH + MLP_IMG_W4;  // 106496
+constexpr int MLP_BIAS_FLOATS = 3 * 128 + 16;
+
+struct MlpNorm { double mu_in[6], inv_sd_in[6], mu_out[6], sd_out[6]; };
+
+cudaError_t launch_mlp_pack(const float *params, uint8_t *img, float *bias, float *wt,
+                            float *wn, cudaStream_t st);
+// err: device word that receives BL_DEVERR_* flags of bounded waits.
+cudaError_t launch_mlp_forward(Soa<float> z, int64_t n, const uint8_t *img, const float *bias,
+                               const MlpNorm &nrm, int num_sms, unsigned *err, cudaStream_t st);
+cudaError_t mlp_forward_configure();
+
+// Partial-gradient row stride (floats) of the training kernels, padded for
+// 16-byte aligned vector stores.
+constexpr int MLP_PSTRIDE = 51208;
+int mlp_grad_blocks(int64_t count);
+
+// Minibatch MSE gradient with the SIMT kernels (mlp_train.cu): in/out are
+// coordinate-major [6][ld] FP32; partials: mlp_grad_blocks(batch) rows of
+// MLP_PSTRIDE floats; loss_partials: one double per block.
+cudaError_t launch_mlp_grad(const float *in, const float *out, int64_t ld, const int64_t *idx,
+                            int64_t batch, const float *wt, const float *wn, const MlpNorm &nrm,
+                            float *partials, double *loss_partials, int *nblocks_out,
+                            cudaStream_t st);
+// Sum partial gradients; if step > 0 apply Adam with bias correction for
+// step t = step. grad_out (device, NPARAM) and loss_out (device) optional.
+cudaError_t launch_mlp_reduce_adam(const float *partials, int nblocks, const double *loss_partials,
+                                   int64_t batch, float *params, float *m, float *v, double lr,
+                                   double b1, double b2, double eps, int step, float *loss_out,
+                                   float *grad_out, cudaStream_t st);
+cudaError_t launch_mlp_loss(const float *in, const float *out, int64_t ld, const int64_t *idx,
+                            int64_t count, const float *wt, const float *wn, const MlpNorm &nrm,
+                            double *loss_partials, int *nblocks_out, cudaStream_t st);
+cudaError_t launch_loss_finalize(const double *loss_partials, int nblocks, int64_t count,
+                                 double *loss_out, cudaStream_t st);
+// lam <- J_F(zin)^T lam for every particle (raw coordinates on both sides).
+cudaError_t launch_mlp_vjp(Soa<float> zin, Soa<float> lam, int64_t n, const float *wt,
+                           const float *wn, const MlpNorm &nrm, cudaStream_t st);
+
+
+}  // namespace bl

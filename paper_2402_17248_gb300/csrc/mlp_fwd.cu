@@ -1,0 +1,377 @@
+// Stage surrogate inference: the MLP F = L4 o s o L3 o s o L2 o s o L1 o s o L0
+// of Sec. 3 (widths 6-128-128-128-128-6, s = GELU in tanh form) applied to
+// every particle in place (Sec. 4.3: in-situ inference on device-resident
+// particles, with the normalise / de-normalise data preparation fused).
+//
+// Design (one persistent CTA per SM, two 128-particle tile slots per CTA):
+//  * The five weight matrices (BF16, ~104 KB) are copied once per CTA into
+//    shared memory by bulk async copies and stay there for all tiles. They
+//    are the B operand of every MMA, in the K-major no-swizzle core-matrix
+//    layout prepared by the pack kernel.
+//  * A tile's activations never leave the SM: each layer's accumulator
+//    D[128 particles x N] is in tensor memory, the epilogue warps read it
+//    (tcgen05.ld), add the bias, apply GELU, round to BF16 and write the
+//    result back into tensor memory (tcgen05.st) as the A operand of the next
+//    layer's MMA (A-from-TMEM form), so shared memory carries only weights.
+//  * Each of the two warpgroups owns one tile slot (accumulator 128 columns,
+//    activation 64 columns of TMEM) and one elected thread issues its MMAs;
+//    the two slots run out of phase, so one tile's MMAs overlap the other
+//    tile's epilogue.
+//  * Inputs are normalised in FP64 and rounded to BF16; the 7th input column
+//    holds 1.0 so the first layer's bias rides in the K padding. Outputs are
+//    de-normalised in FP64 and stored as FP32.
+//  * Hidden activations are stored as 2*GELU(x) = x (1 + tanh(u)) and the
+//    next layer's weights are pre-scaled by 1/2 (exact in BF16).
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "internal.h"
+#include "tc.cuh"
+
+namespace bl {
+
+namespace {
+
+constexpr int SLOTS = 2;
+constexpr int THREADS = 128 * SLOTS;
+constexpr uint32_t OFF_W0 = 0;
+constexpr uint32_t OFF_W1 = OFF_W0 + MLP_IMG_W0;
+constexpr uint32_t OFF_W4 = OFF_W1 + 3 * MLP_IMG_WH;
+constexpr uint32_t OFF_BIAS = MLP_IMG_BYTES;                      // 106496
+constexpr uint32_t OFF_BAR = OFF_BIAS + MLP_BIAS_FLOATS * 4;      // 108096
+constexpr uint32_t OFF_SLOT = OFF_BAR + 8 * (1 + SLOTS);
+// Dynamic shared memory requested: more than half of the SM's 228 KB so that
+// exactly one CTA (which owns all 512 TMEM columns) is resident per SM.
+constexpr uint32_t SMEM_BYTES = 120 * 1024;
+
+constexpr float GELU_C0 = 0.7978845608028654f;               // sqrt(2/pi)
+constexpr float GELU_C1 = 0.7978845608028654f * 0.044715f;
+
+// Byte offset of element (n, k) of an [N x K] K-major BF16 block in the
+// no-swizzle core-matrix layout: 8x8 core matrices of 128 contiguous bytes,
+// adjacent along K at 128 bytes, adjacent along N at (K/8)*128 bytes.
+__host__ __device__ inline uint32_t img_off(int n, int k, int K) {
+  return (uint32_t)((n >> 3) * (K / 8) * 128 + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2);
+}
+
+BL_DEV float gelu2(float x) {
+  // 2 * GELU(x) = x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3)))
+  const float u = x * fmaf(GELU_C1, x * x, GELU_C0);
+  return fmaf(x, tc::tanh_approx(u), x);
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__restrict__ img,
+                   const float *__restrict__ bias, MlpNorm nrm, unsigned *err) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  float *sB = reinterpret_cast<float *>(smem + OFF_BIAS);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + OFF_SLOT);
+  const uint32_t sbase = tc::smem_u32(smem);
+  const uint32_t bar_w = sbase + OFF_BAR;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int slot = warp >> 2, wq = warp & 3;
+  const uint32_t bar_m = sbase + OFF_BAR + 8 * (1 + slot);
+
+  if (tid == 0) {
+    tc::mbar_init(bar_w, 1);
+    for (int s = 0; s < SLOTS; ++s) tc::mbar_init(sbase + OFF_BAR + 8 * (1 + s), 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tc::smem_u32(tslot), 512);
+    tc::tmem_relinquish();
+  }
+  for (int i = tid; i < MLP_BIAS_FLOATS; i += THREADS) sB[i] = bias[i];
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = *tslot;
+  if (tid == 0) {
+    tc::mbar_expect_tx(bar_w, MLP_IMG_BYTES);
+    tc::bulk_g2s(sbase + OFF_W0, img + OFF_W0, MLP_IMG_W0, bar_w);
+    for (int l = 0; l < 3; ++l)
+      tc::bulk_g2s(sbase + OFF_W1 + l * MLP_IMG_WH, img + OFF_W1 + l * MLP_IMG_WH, MLP_IMG_WH, bar_w);
+    tc::bulk_g2s(sbase + OFF_W4, img + OFF_W4, MLP_IMG_W4, bar_w);
+  }
+  bool ok = tc::mbar_wait(bar_w, 0, BL_DEVERR_TMA_TIMEOUT, err);
+
+  const uint32_t lane_base = (uint32_t)(wq * 32) << 16;
+  const uint32_t t_acc = tmem + lane_base + slot * 256;
+  const uint32_t t_act = t_acc + 128;
+  const uint32_t d_acc = tmem + slot * 256;  // lane 0 addresses for the MMA
+  const uint32_t d_act = d_acc + 128;
+  const bool issuer = (tid & 127) == 0;
+  constexpr uint32_t ID_H = tc::idesc_bf16(128, 128);
+  constexpr uint32_t ID_O = tc::idesc_bf16(128, 16);
+  uint32_t phase = 0;
+
+  ok = __all_sync(0xffffffffu, ok);
+  for (int64_t tile = (int64_t)blockIdx.x * SLOTS + slot; tile < ntiles;
+       tile += (int64_t)gridDim.x * SLOTS) {
+    const int64_t p = tile * 128 + wq * 32 + lane;
+    const bool valid = p < n;
+    // a failed wait anywhere in the warpgroup stops all of its threads together
+    if (!tc::named_bar_and(1 + slot, 128, ok)) break;
+    // ---- prologue: FP64 normalisation, BF16 input row in TMEM
+    {
+      float xn[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        const float v = valid ? z.c[c][p] : 0.0f;
+        xn[c] = (float)(((double)v - nrm.mu_in[c]) * nrm.inv_sd_in[c]);
+      }
+      uint32_t a[8];
+      a[0] = tc::pack_bf16x2(xn[0], xn[1]);
+      a[1] = tc::pack_bf16x2(xn[2], xn[3]);
+      a[2] = tc::pack_bf16x2(xn[4], xn[5]);
+      a[3] = tc::pack_bf16x2(1.0f, 0.0f);
+      a[4] = a[5] = a[6] = a[7] = 0u;
+      tc::tmem_st8(t_act, a);
+      tc::tmem_st_wait();
+      tc::fence_before();
+    }
+    // ---- five layers
+    bool go = true;
+#pragma unroll 1
+    for (int l = 0; l < 5; ++l) {
+      go = tc::named_bar_and(1 + slot, 128, ok);
+      if (!go) break;
+      if (issuer) {
+        tc::fence_after();
+        if (l == 0) {
+          tc::mma_ts(d_acc, d_act, tc::sdesc(sbase + OFF_W0, 128, 256), ID_H, 0);
+        } else {
+          const uint32_t wb = (l < 4) ? sbase + OFF_W1 + (l - 1) * MLP_IMG_WH : sbase + OFF_W4;
+          const uint32_t id = (l < 4) ? ID_H : ID_O;
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            tc::mma_ts(d_acc, d_act + 8 * j, tc::sdesc(wb + 256 * j, 128, 2048), id, j > 0);
+        }
+        tc::mma_commit(bar_m);
+      }
+      __syncwarp();
+      ok = tc::mbar_wait(bar_m, phase, BL_DEVERR_MMA_TIMEOUT, err);
+      ok = __all_sync(0xffffffffu, ok);
+      phase ^= 1;
+      tc::fence_after();
+      if (!ok) continue;  // the next barrier stops the warpgroup
+      if (l < 4) {
+        const float *b = (l == 0) ? nullptr : sB + (l - 1) * 128;
+#pragma unroll 1
+        for (int ch = 0; ch < 4; ++ch) {
+          uint32_t r[32];
+          tc::tmem_ld32(t_acc + 32 * ch, r);
+          tc::tmem_ld_wait();
+          uint32_t o[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            float x0 = __uint_as_float(r[2 * j]), x1 = __uint_as_float(r[2 * j + 1]);
+            if (b) {
+              x0 += b[32 * ch + 2 * j];
+              x1 += b[32 * ch + 2 * j + 1];
+            }
+            o[j] = tc::pack_bf16x2(gelu2(x0), gelu2(x1));
+          }
+          tc::tmem_st16(t_act + 16 * ch, o);
+        }
+        tc::tmem_st_wait();
+        tc::fence_before();
+      } else {
+        uint32_t r[8];
+        tc::tmem_ld8(t_acc, r);
+        tc::tmem_ld_wait();
+        if (valid) {
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            const float yv = __uint_as_float(r[c]) + sB[384 + c];
+            z.c[c][p] = (float)fma((double)yv, nrm.sd_out[c], nrm.mu_out[c]);
+          }
+        }
+        tc::fence_before();
+      }
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+// Parameters (flat FP32, layout of mlp_w_off/mlp_b_off) -> BF16 UMMA image,
+// FP32 bias block, and BF16-rounded FP32 copies in [in][out] (wt) and
+// [out][in] (wn) layouts for the SIMT kernels.
+__global__ void mlp_pack_kernel(const float *__restrict__ P, uint8_t *__restrict__ img,
+                                float *__restrict__ bias, float *__restrict__ wt,
+                                float *__restrict__ wn) {
+  const int widths[6] = {6, 128, 128, 128, 128, 6};
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int stride = gridDim.x * blockDim.x;
+  __nv_bfloat16 *im = reinterpret_cast<__nv_bfloat16 *>(img);
+  // layer 0 image: N = 128, K = 16 (6 inputs, bias at column 6, zeros)
+  for (int i = tid; i < 128 * 16; i += stride) {
+    const int nn = i / 16, k = i % 16;
+    float v = 0.f;
+    if (k < 6) v = P[0 + nn * 6 + k];
+    else if (k == 6) v = P[768 + nn];
+    im[img_off(nn, k, 16) / 2] = __float2bfloat16_rn(v);
+  }
+  // hidden layers 1..3: N = K = 128, weights scaled by 1/2
+  const int woff[3] = {896, 17408, 33920};
+  for (int l = 0; l < 3; ++l) {
+    __nv_bfloat16 *base = im + (MLP_IMG_W0 + l * MLP_IMG_WH) / 2;
+    for (int i = tid; i < 128 * 128; i += stride) {
+      const int nn = i / 128, k = i % 128;
+      base[img_off(nn, k, 128) / 2] = __float2bfloat16_rn(0.5f * P[woff[l] + i]);
+    }
+  }
+  // layer 4: N = 16 (6 outputs, zero rows), K = 128, scaled by 1/2
+  {
+    __nv_bfloat16 *base = im + (MLP_IMG_W0 + 3 * MLP_IMG_WH) / 2;
+    for (int i = tid; i < 16 * 128; i += stride) {
+      const int nn = i / 128, k = i % 128;
+      const float v = nn < 6 ? 0.5f * P[50432 + nn * 128 + k] : 0.f;
+      base[img_off(nn, k, 128) / 2] = __float2bfloat16_rn(v);
+    }
+  }
+  for (int i = tid; i < MLP_BIAS_FLOATS; i += stride) {
+    float v = 0.f;
+    if (i < 384) v = P[(i < 128 ? 17280 : (i < 256 ? 33792 : 50304)) + (i & 127)];
+    else if (i < 390) v = P[51200 + (i - 384)];
+    bias[i] = v;
+  }
+  // SIMT copies: BF16-rounded weights (unscaled), exact FP32 biases
+  for (int l = 0; l < 5; ++l) {
+    const int fi = widths[l], fo = widths[l + 1];
+    const int wo = (l == 0) ? 0 : (l == 1 ? 896 : (l == 2 ? 17408 : (l == 3 ? 33920 : 50432)));
+    const int bo = wo + fi * fo;
+    for (int i = tid; i < fi * fo; i += stride) {
+      const int o = i / fi, k = i % fi;
+      const float w = __bfloat162float(__float2bfloat16_rn(P[wo + i]));
+      wn[wo + i] = w;
+      wt[wo + k * fo + o] = w;
+    }
+    for (int i = tid; i < fo; i += stride) {
+      wn[bo + i] = P[bo + i];
+      wt[bo + i] = P[bo + i];
+    }
+  }
+}
+
+// Diagnostic: one MMA D = A * B^T with A [128 x K] (BF16, row-major, placed
+// in TMEM) and B [N x K] (BF16, row-major, staged into shared memory with
+// core-matrix strides ks (along K) and ns (along N)), using descriptor fields
+// lbo and sbo; D FP32 [128 x N] row-major in global memory. All shared-memory
+// addresses stay inside the 64 KB dynamic buffer for N, K <= 128 and strides
+// <= 2048 bytes.
+__global__ void __launch_bounds__(128, 1)
+umma_probe_kernel(const __nv_bfloat16 *__restrict__ A, const __nv_bfloat16 *__restrict__ B,
+                  float *__restrict__ D, int N, int K, uint32_t ks, uint32_t ns, uint32_t lbo,
+                  uint32_t sbo) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t slot;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  for (int i = tid; i < 32768; i += 128) reinterpret_cast<uint16_t *>(sm)[i] = 0;
+  __syncthreads();
+  for (int i = tid; i < N * K; i += 128) {
+    const int nn = i / K, k = i % K;
+    const uint32_t off = (uint32_t)((nn >> 3) * ns + (k >> 3) * ks + (nn & 7) * 16 + (k & 7) * 2);
+    if (off + 2 <= 65536u) *reinterpret_cast<__nv_bfloat16 *>(sm + off) = B[i];
+  }
+  if (tid == 0) {
+    tc::mbar_init(tc::smem_u32(&bar), 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tc::smem_u32(&slot), 256);
+    tc::tmem_relinquish();
+  }
+  tc::fence_proxy_async();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = slot;
+  const uint32_t lb = (uint32_t)(warp * 32) << 16;
+  for (int c0 = 0; c0 < K / 2; c0 += 8) {
+    uint32_t a[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int k = 2 * (c0 + j);
+      const uint32_t lo = __bfloat16_as_ushort(A[tid * K + k]);
+      const uint32_t hi = __bfloat16_as_ushort(A[tid * K + k + 1]);
+      a[j] = lo | (hi << 16);
+    }
+    tc::tmem_st8(tmem + lb + 128 + c0, a);
+  }
+  tc::tmem_st_wait();
+  tc::fence_before();
+  __syncthreads();
+  if (tid == 0) {
+    tc::fence_after();
+    for (int j = 0; j < K / 16; ++j)
+      tc::mma_ts(tmem, tmem + 128 + 8 * j, tc::sdesc(tc::smem_u32(sm) + 2 * ks * j, lbo, sbo),
+                 tc::idesc_bf16(128, N), j > 0);
+    tc::mma_commit(tc::smem_u32(&bar));
+  }
+  __syncwarp();
+  const bool ok = __all_sync(0xffffffffu,
+                             tc::mbar_wait(tc::smem_u32(&bar), 0, BL_DEVERR_MMA_TIMEOUT, nullptr));
+  tc::fence_after();
+  if (ok) {
+    for (int c0 = 0; c0 < N; c0 += 8) {
+      uint32_t r[8];
+      tc::tmem_ld8(tmem + lb + c0, r);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int j = 0; j < 8; ++j) D[tid * N + c0 + j] = __uint_as_float(r[j]);
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (warp == 0) tc::tmem_dealloc(tmem, 256);
+}
+
+}  // namespace
+
+cudaError_t mlp_forward_configure() {
+  return cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)SMEM_BYTES);
+}
+
+cudaError_t launch_mlp_pack(const float *params, uint8_t *img, float *bias, float *wt, float *wn,
+                            cudaStream_t st) {
+  mlp_pack_kernel<<<64, 256, 0, st>>>(params, img, bias, wt, wn);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_forward(Soa<float> z, int64_t n, const uint8_t *img, const float *bias,
+                               const MlpNorm &nrm, int num_sms, unsigned *err, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t ntiles = (n + 127) / 128;
+  int64_t grid = (ntiles + SLOTS - 1) / SLOTS;
+  if (grid > num_sms) grid = num_sms;
+  mlp_forward_kernel<<<(unsigned)grid, THREADS, SMEM_BYTES, st>>>(z, n, ntiles, img, bias, nrm, err);
+  return cudaGetLastError();
+}
+
+}  // namespace bl
+
+// Diagnostic entry point (declared in include/bl_debug.h).
+extern "C" int bl_debug_umma_probe(const void *A, const void *B, float *D, int N, int K,
+                                   uint32_t ks, uint32_t ns, uint32_t lbo, uint32_t sbo,
+                                   void *stream) {
+  if (!(N == 16 || N == 32 || N == 64 || N == 128) || !(K == 16 || K == 32 || K == 64 || K == 128))
+    return 1;
+  if (ks > 2048 || ns > 2048 || (ks % 16) || (ns % 16) || ks < 128 || ns < 128) return 1;
+  static bool configured = false;
+  if (!configured) {
+    if (cudaFuncSetAttribute(bl::umma_probe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             65536) != cudaSuccess)
+      return 2;
+    configured = true;
+  }
+  bl::umma_probe_kernel<<<1, 128, 65536, (cudaStream_t)stream>>>(
+      (const __nv_bfloat16 *)A, (const __nv_bfloat16 *)B, D, N, K, ks, ns, lbo, sbo);
+  return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}

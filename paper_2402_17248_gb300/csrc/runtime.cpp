@@ -1,0 +1,356 @@
+// Host runtime: errors, device context, workspaces, FP64 element matrices
+// and the FP64 reference-particle track of a plasma stage.
+#include "runtime.h"
+
+#include <cmath>
+#include <cstdio>
+
+namespace bl {
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_last_error;
+
+bl_status set_error(bl_status st, const std::string &msg) {
+  g_last_error = msg;
+  return st;
+}
+
+bl_status cuda_error(cudaError_t e, const char *what) {
+  cudaGetLastError();  // clear a sticky-free error so later calls start clean
+  const bl_status st = (e == cudaErrorMemoryAllocation) ? BL_ERR_OOM : BL_ERR_CUDA;
+  return set_error(st, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// ----------------------------------------------------------------- context
+static std::mutex g_ctx_mu;
+static std::map<int, std::unique_ptr<DevCtx>> g_ctx;
+
+bl_status current_ctx(DevCtx **out) {
+  int dev = -1;
+  BL_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_ctx_mu);
+  auto &p = g_ctx[dev];
+  if (!p) {
+    auto c = std::make_unique<DevCtx>();
+    c->device = dev;
+    cudaDeviceProp prop;
+    BL_CUDA(cudaGetDeviceProperties(&prop, dev));
+    c->num_sms = prop.multiProcessorCount;
+    c->arch_ok = (prop.major == 10 && prop.minor == 3);
+    if (c->arch_ok) {
+      BL_CUDA(cudaMalloc(&c->err_word, sizeof(unsigned)));
+      BL_CUDA(cudaMemset(c->err_word, 0, sizeof(unsigned)));
+    }
+    p = std::move(c);
+  }
+  if (!p->arch_ok)
+    return set_error(BL_ERR_UNSUPPORTED_ARCH,
+                     "this library is built for sm_103a (GB300); the current device is not");
+  *out = p.get();
+  return BL_OK;
+}
+
+// -------------------------------------------------------------- workspace
+static std::mutex g_ws_mu;
+static std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
+
+bl_status ws_get(cudaStream_t st, WsSlot slot, size_t bytes, void **out) {
+  int dev = -1;
+  BL_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  Workspace &w = g_ws[{dev, st}];
+  if (bytes == 0) bytes = 256;
+  if (w.bytes[slot] < bytes) {
+    if (w.ptr[slot]) {
+      BL_CUDA(cudaStreamSynchronize(st));
+      BL_CUDA(cudaFree(w.ptr[slot]));
+      w.ptr[slot] = nullptr;
+      w.bytes[slot] = 0;
+    }
+    const size_t want = bytes + bytes / 4;
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) return cuda_error(e, "workspace allocation");
+    w.ptr[slot] = p;
+    w.bytes[slot] = want;
+  }
+  *out = w.ptr[slot];
+  return BL_OK;
+}
+
+// ---------------------------------------------------------------- matrices
+Mat6 mat_identity() {
+  Mat6 M{};
+  for (int i = 0; i < 6; ++i) M[i * 6 + i] = 1.0;
+  return M;
+}
+
+Mat6 mat_mul(const Mat6 &A, const Mat6 &B) {
+  Mat6 C{};
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < 6; ++k) s += A[i * 6 + k] * B[k * 6 + j];
+      C[i * 6 + j] = s;
+    }
+  return C;
+}
+
+Mat6 mat_transpose(const Mat6 &A) {
+  Mat6 T{};
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) T[j * 6 + i] = A[i * 6 + j];
+  return T;
+}
+
+// 2x2 solution matrix of x'' = -kk x over length L (row-major m[4]).
+static void plane(double L, double kk, double m[4]) {
+  if (kk > 0.0) {
+    const double w = std::sqrt(kk), c = std::cos(w * L), s = std::sin(w * L);
+    m[0] = c; m[1] = s / w; m[2] = -w * s; m[3] = c;
+  } else if (kk < 0.0) {
+    const double w = std::sqrt(-kk), c = std::cosh(w * L), s = std::sinh(w * L);
+    m[0] = c; m[1] = s / w; m[2] = w * s; m[3] = c;
+  } else {
+    m[0] = 1.0; m[1] = L; m[2] = 0.0; m[3] = 1.0;
+  }
+}
+
+// d/dkk of plane(L, kk).
+static void dplane(double L, double kk, double m[4]) {
+  if (kk > 0.0) {
+    const double w = std::sqrt(kk), c = std::cos(w * L), s = std::sin(w * L), dw = 0.5 / w;
+    m[0] = -L * s * dw;
+    m[1] = (L * c / w - s / (w * w)) * dw;
+    m[2] = (-s - w * L * c) * dw;
+    m[3] = -L * s * dw;
+  } else if (kk < 0.0) {
+    const double w = std::sqrt(-kk), c = std::cosh(w * L), s = std::sinh(w * L), dw = -0.5 / w;
+    m[0] = L * s * dw;
+    m[1] = (L * c / w - s / (w * w)) * dw;
+    m[2] = (s + w * L * c) * dw;
+    m[3] = L * s * dw;
+  } else {
+    m[0] = -0.5 * L * L; m[1] = -L * L * L / 6.0; m[2] = -L; m[3] = -0.5 * L * L;
+  }
+}
+
+Mat6 element_matrix(const bl_element &e, double k, double bg) {
+  Mat6 M = mat_identity();
+  const double L = e.L;
+  if (e.kind == BL_DRIFT || (e.kind == BL_SBEND && e.angle == 0.0)) {
+    M[0 * 6 + 1] = L;
+    M[2 * 6 + 3] = L;
+    M[4 * 6 + 5] = L / (bg * bg);
+  } else if (e.kind == BL_QUAD) {
+    double a[4], b[4];
+    plane(L, k, a);
+    plane(L, -k, b);
+    M[0] = a[0]; M[1] = a[1]; M[6] = a[2]; M[7] = a[3];
+    M[14] = b[0]; M[15] = b[1]; M[20] = b[2]; M[21] = b[3];
+    M[4 * 6 + 5] = L / (bg * bg);
+  } else if (e.kind == BL_SBEND) {
+    const double th = e.angle, h = th / L, beta = bg / std::sqrt(1.0 + bg * bg);
+    const double C = std::cos(th), S = std::sin(th);
+    M[0 * 6 + 0] = C;
+    M[0 * 6 + 1] = S / h;
+    M[0 * 6 + 5] = -(1.0 - C) / (h * beta);
+    M[1 * 6 + 0] = -h * S;
+    M[1 * 6 + 1] = C;
+    M[1 * 6 + 5] = -S / beta;
+    M[2 * 6 + 3] = L;
+    M[4 * 6 + 0] = S / beta;
+    M[4 * 6 + 1] = (1.0 - C) / (h * beta);
+    M[4 * 6 + 5] = L / (bg * bg) - (th - S) / (h * beta * beta);
+  }
+  return M;
+}
+
+Mat6 element_dmatrix_dk(const bl_element &e, double k, double bg) {
+  (void)bg;
+  Mat6 D{};
+  if (e.kind != BL_QUAD) return D;
+  double a[4], b[4];
+  dplane(e.L, k, a);
+  dplane(e.L, -k, b);
+  D[0] = a[0]; D[1] = a[1]; D[6] = a[2]; D[7] = a[3];
+  D[14] = -b[0]; D[15] = -b[1]; D[20] = -b[2]; D[21] = -b[3];
+  return D;
+}
+
+// ------------------------------------------------------- reference track
+bl_status stage_track(const bl_element &e, double gamma_in, int want, StageTrack *out) {
+  BL_CHECK(e.kind == BL_PLASMA, "element is not a plasma stage");
+  BL_CHECK(e.nsteps >= 1 && e.nsteps <= (1 << 20), "plasma stage needs 1 <= nsteps <= 2^20");
+  BL_CHECK(e.L > 0.0 && std::isfinite(e.L), "plasma stage length must be positive");
+  BL_CHECK(e.n0_cm3 > 0.0 && std::isfinite(e.n0_cm3), "plasma density must be positive");
+  BL_CHECK(std::isfinite(e.E0_Vpm) && std::isfinite(e.phi0), "wake amplitude/phase not finite");
+  BL_CHECK(gamma_in > 1.0 && std::isfinite(gamma_in), "reference gamma must exceed 1");
+  const double n0 = e.n0_cm3 * 1.0e6;
+  const double kp = std::sqrt(n0 * Consts::E * Consts::E / (Consts::EPS0 * Consts::ME)) / Consts::C;
+  const double g = e.E0_Vpm / Consts::MEC2_EV;
+  const double K0 = 0.5 * g * kp;
+  const int n = e.nsteps;
+  const double h = e.L / n;
+  StageConsts &c = out->c;
+  c.kp = kp; c.g = g; c.K0 = K0; c.h = h; c.nsteps = n;
+  c.gamma_in = gamma_in;
+  c.bg_in = std::sqrt(gamma_in * gamma_in - 1.0);
+  auto wof = [](double uz) { return 1.0 / (uz * (std::sqrt(1.0 + uz * uz) + uz)); };
+  auto f = [&](double zeta, double uz, double &dz, double &du) {
+    const double w = wof(uz);
+    dz = -w;
+    du = (1.0 + w) * g * std::cos(kp * zeta);
+  };
+  double zeta = e.phi0 / kp, uz = c.bg_in;
+  if (want == BL_F32) out->table32.assign((size_t)n * 16, 0.0f);
+  if (want == BL_F64) out->table64.assign((size_t)n * 16, 0.0);
+  for (int s = 0; s < n; ++s) {
+    double z[4], u[4], kz[4], ku[4];
+    z[0] = zeta; u[0] = uz;
+    f(z[0], u[0], kz[0], ku[0]);
+    z[1] = zeta + 0.5 * h * kz[0]; u[1] = uz + 0.5 * h * ku[0];
+    f(z[1], u[1], kz[1], ku[1]);
+    z[2] = zeta + 0.5 * h * kz[1]; u[2] = uz + 0.5 * h * ku[1];
+    f(z[2], u[2], kz[2], ku[2]);
+    z[3] = zeta + h * kz[2]; u[3] = uz + h * ku[2];
+    f(z[3], u[3], kz[3], ku[3]);
+    if (want == BL_F32) {
+      float *t = out->table32.data() + (size_t)s * 16;
+      const double phn = kp * z[0];
+      for (int i = 0; i < 4; ++i) {
+        t[4 * i + 0] = (float)u[i];
+        t[4 * i + 1] = (float)wof(u[i]);
+        if (i == 0) {
+          t[2] = (float)std::sin(phn);
+          t[3] = (float)std::cos(phn);
+        } else {
+          t[4 * i + 2] = (float)(kp * (z[i] - z[0]));
+          t[4 * i + 3] = 0.0f;
+        }
+      }
+    } else if (want == BL_F64) {
+      double *t = out->table64.data() + (size_t)s * 16;
+      for (int i = 0; i < 4; ++i) {
+        t[4 * i + 0] = u[i];
+        t[4 * i + 1] = wof(u[i]);
+        t[4 * i + 2] = kp * z[i];
+        t[4 * i + 3] = 0.0;
+      }
+    }
+    zeta += (h / 6.0) * (kz[0] + 2.0 * kz[1] + 2.0 * kz[2] + kz[3]);
+    uz += (h / 6.0) * (ku[0] + 2.0 * ku[1] + 2.0 * ku[2] + ku[3]);
+  }
+  c.uz_ref_out = uz;
+  c.bg_out = uz;
+  c.gamma_out = std::sqrt(1.0 + uz * uz);
+  return BL_OK;
+}
+
+bool bunch_dims_ok(const bl_bunch *b, std::string *why) {
+  if (!b) { *why = "bunch is NULL"; return false; }
+  if (b->n < 0) { *why = "bunch n must be >= 0"; return false; }
+  if (b->dtype != BL_F32 && b->dtype != BL_F64) { *why = "bunch dtype must be BL_F32 or BL_F64"; return false; }
+  if (b->n_bunch < 1) { *why = "n_bunch must be >= 1"; return false; }
+  if (b->n > 0 && (!b->x || !b->px || !b->y || !b->py || !b->t || !b->pt)) {
+    *why = "bunch coordinate pointer is NULL"; return false;
+  }
+  if (b->n_bunch > 1 && (!b->offsets_dev || !b->offsets_host)) {
+    *why = "n_bunch > 1 needs offsets_dev and offsets_host"; return false;
+  }
+  if (b->offsets_host) {
+    if (b->offsets_host[0] != 0 || b->offsets_host[b->n_bunch] != b->n) {
+      *why = "offsets must start at 0 and end at n"; return false;
+    }
+    for (int i = 0; i < b->n_bunch; ++i)
+      if (b->offsets_host[i + 1] < b->offsets_host[i]) { *why = "offsets must be non-decreasing"; return false; }
+    if (!b->offsets_dev) { *why = "offsets_host given without offsets_dev"; return false; }
+  }
+  if (!(b->gamma_ref > 1.0) || !std::isfinite(b->gamma_ref)) { *why = "gamma_ref must exceed 1"; return false; }
+  return true;
+}
+
+bl_status moments_device(const bl_bunch *b, double *out_dev, unsigned long long *nonfinite,
+                         cudaStream_t st) {
+  void *part = nullptr;
+  BL_TRY(ws_get(st, WS_PARTIALS, (size_t)stream_slots(b->n, b->n_bunch) * 28 * sizeof(double), &part));
+  const int64_t *off = b->n_bunch > 1 ? b->offsets_dev : nullptr;
+  if (b->dtype == BL_F32) {
+    Soa<float> z = soa_of<float>(b);
+    BL_CUDA(launch_stream<float>(z, z, b->n, off, b->n_bunch, nullptr, 0, nullptr, false, true,
+                                 (double *)part, st));
+  } else {
+    Soa<double> z = soa_of<double>(b);
+    BL_CUDA(launch_stream<double>(z, z, b->n, off, b->n_bunch, nullptr, 0, nullptr, false, true,
+                                  (double *)part, st));
+  }
+  BL_CUDA(launch_moments_finalize((const double *)part, off, b->n_bunch, b->n, out_dev, nonfinite, st));
+  return BL_OK;
+}
+
+void propagate_moments(const Mat6 &M, const double *in, double *out) {
+  double S[36], T[36];
+  int j = 0;
+  for (int a = 0; a < 6; ++a)
+    for (int c = a; c < 6; ++c) {
+      S[a * 6 + c] = S[c * 6 + a] = in[7 + j];
+      ++j;
+    }
+  out[0] = in[0];
+  for (int i = 0; i < 6; ++i) {
+    double s = 0.0;
+    for (int k = 0; k < 6; ++k) s += M[i * 6 + k] * in[1 + k];
+    out[1 + i] = s;
+  }
+  for (int i = 0; i < 6; ++i)
+    for (int c = 0; c < 6; ++c) {
+      double s = 0.0;
+      for (int k = 0; k < 6; ++k) s += M[i * 6 + k] * S[k * 6 + c];
+      T[i * 6 + c] = s;
+    }
+  j = 0;
+  for (int a = 0; a < 6; ++a)
+    for (int c = a; c < 6; ++c) {
+      double s = 0.0;
+      for (int k = 0; k < 6; ++k) s += T[a * 6 + k] * M[c * 6 + k];
+      out[7 + j] = s;
+      ++j;
+    }
+}
+
+}  // namespace bl
+
+bl_lattice_s::~bl_lattice_s() {
+  if (plan.d_tables) cudaFree(plan.d_tables);
+  if (plan.d_mats) cudaFree(plan.d_mats);
+}
+
+extern "C" {
+
+const char *bl_last_error_message(void) { return bl::g_last_error.c_str(); }
+
+const char *bl_version(void) { return "bl 0.1 (sm_103a)"; }
+
+bl_status bl_poll_device_errors(void) {
+  bl::DevCtx *ctx = nullptr;
+  BL_TRY(bl::current_ctx(&ctx));
+  BL_CUDA(cudaDeviceSynchronize());
+  unsigned v = 0;
+  BL_CUDA(cudaMemcpy(&v, ctx->err_word, sizeof(v), cudaMemcpyDeviceToHost));
+  if (v) {
+    BL_CUDA(cudaMemset(ctx->err_word, 0, sizeof(unsigned)));
+    return bl::set_error(BL_ERR_TIMEOUT, "a device-side bounded wait gave up (flags " +
+                                             std::to_string(v) + ")");
+  }
+  return BL_OK;
+}
+
+bl_status bl_reference_exit(const bl_element *stage, double gamma_in, double *gamma_out) {
+  BL_CHECK(stage && gamma_out, "NULL argument");
+  bl::StageTrack tr;
+  BL_TRY(bl::stage_track(*stage, gamma_in, -1, &tr));
+  *gamma_out = tr.c.gamma_out;
+  return BL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,75 @@
+"""The C-ABI library loads and exports every declared symbol; host-only calls
+and argument checks (no GPU needed)."""
+import math
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2402_17248_gb300 import bl
+from oracle import wake
+from synth import lattice
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2402_17248_gb300 import build
+    build.build()
+
+
+def _declared():
+    names = set()
+    for h in ("bl.h", "bl_debug.h"):
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"\b(bl_[a-z0-9_]+)\s*\(", src):
+            names.add(m.group(1))
+    return names
+
+
+def test_exports_every_declared_symbol():
+    names = _declared()
+    assert len(names) >= 20
+    out = subprocess.run(["nm", "-D", "--defined-only", bl.LIB_PATH], capture_output=True,
+                         text=True).stdout
+    exported = set(re.findall(r"\bT (bl_[a-z0-9_]+)", out))
+    missing = names - exported
+    assert not missing, missing
+    L = bl.lib()
+    for n in names:
+        assert hasattr(L, n)
+
+
+def test_reference_exit_matches_oracle():
+    st = lattice.plasma(400)
+    for g in (1957.9511835591836, 6111.38, 30000.0):
+        want = wake.reference_exit(wake.Stage(nsteps=400), g)[0]
+        got = bl.bl_reference_exit(st, g)
+        assert abs(got / want - 1) < 1e-12
+
+
+def test_lattice_create_counts_and_validation():
+    L = bl.Lattice(lattice.staged_beamline(2, 10))
+    assert L.num_elements == 36
+    assert L.num_quads == 8
+    with pytest.raises(bl.BlError) as e:
+        bl.Lattice([{"kind": "plasma", "L": 0.3, "nsteps": 0, "n0_cm3": 1e17,
+                     "E0_Vpm": 1e10, "phi0": 0.7}])
+    assert e.value.status == bl.BL_ERR_INVALID_ARG
+    with pytest.raises(bl.BlError):
+        bl.Lattice([{"kind": "quad", "L": 0.1, "k": float("nan")}])
+    with pytest.raises(bl.BlError):
+        bl.Lattice([{"kind": "quad", "L": 0.1, "k": 1.0, "per_bunch_k": [1.0, 2.0]}])
+    with pytest.raises(bl.BlError):
+        bl.bl_reference_exit(lattice.plasma(10), 0.5)
+
+
+def test_per_bunch_lattice():
+    els = [{"kind": "quad", "L": 0.1, "k": 30.0, "per_bunch_k": [20.0, 40.0, 60.0]},
+           {"kind": "drift", "L": 1.0}]
+    L = bl.Lattice(els, n_bunch_k=3)
+    assert L.num_quads == 1

@@ -1,0 +1,168 @@
+"""GPU parity of the MLP surrogate: tcgen05 inference and the training /
+gradient kernels against the FP64 oracle with the same BF16-valued weights."""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_util import KEYS, as_f32, from_bunch, to_bunch
+from oracle import mlp, moments
+from synth.bunch import BunchRecipe, gaussian_bunch, mlp_init
+
+pytestmark = pytest.mark.gpu
+WIDTHS = [6, 128, 128, 128, 128, 6]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    from paper_2402_17248_gb300 import bl
+    bl.lib()
+
+
+def _bunch(n, seed=0):
+    z, g = gaussian_bunch(BunchRecipe(n=n, seed=seed))
+    return as_f32([z[k] for k in KEYS]), g
+
+
+def _net(seed, z, out_shift=0.0):
+    Ws, bs = mlp_init(WIDTHS, seed)
+    Z = np.stack(z, axis=1)
+    mu, sd = Z.mean(axis=0), Z.std(axis=0)
+    return Ws, bs, mu, sd, mu + out_shift * sd, sd * 1.5
+
+
+def _oracle_surrogate(Ws, bs, mu, sd, mo, so):
+    Wr = [mlp.bf16_round(np.asarray(W, dtype=np.float32).astype(np.float64)) for W in Ws]
+    br = [np.asarray(b, dtype=np.float32).astype(np.float64) for b in bs]
+    return mlp.Surrogate(Wr, br, mu, sd, mo, so)
+
+
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 257, 10000, 300001])
+def test_inference_matches_oracle(n):
+    from paper_2402_17248_gb300 import bl
+    z, g = _bunch(max(n, 2), seed=n)
+    z = [c[:n] for c in z]
+    Ws, bs, mu, sd, mo, so = _net(3, _bunch(5000, 1)[0], 0.3)
+    sur = bl.Surrogate(Ws, bs, mu, sd, mo, so)
+    b = to_bunch(z, g)
+    bl.bl_surrogate_apply(sur, b)
+    got = from_bunch(b)
+    bl.bl_poll_device_errors()
+    osur = _oracle_surrogate(Ws, bs, mu, sd, mo, so)
+    want_bf = osur.apply(z, bf16=True)
+    want_64 = osur.apply(z, bf16=False)
+    e_bf = max(float(np.max(np.abs(a - w))) / s for a, w, s in zip(got, want_bf, so))
+    e_64 = max(float(np.max(np.abs(a - w))) / s for a, w, s in zip(got, want_64, so))
+    print("n=%d max |gpu - oracle| / sd_out: bf16-emulating %.3e, fp64 %.3e" % (n, e_bf, e_64))
+    assert e_bf < 2e-3
+    if n >= 10000:
+        dg = moments.moments28(got)
+        dw = moments.moments28(want_64)
+        Sg, Sw = moments.sigma_matrix(dg), moments.sigma_matrix(dw)
+        rel = np.max(np.abs(np.diag(Sg) / np.diag(Sw) - 1))
+        print("  output second moments, relative to the FP64 network: %.3e" % rel)
+        assert rel < 2e-3
+
+
+def test_inference_repeatable_and_inplace_tail():
+    from paper_2402_17248_gb300 import bl
+    import torch
+    z, g = _bunch(1000, seed=4)
+    Ws, bs, mu, sd, mo, so = _net(5, z)
+    sur = bl.Surrogate(Ws, bs, mu, sd, mo, so)
+    # a 997-particle view into a longer buffer: the 3 trailing values stay intact
+    coords = [torch.tensor(c, dtype=torch.float32, device="cuda") for c in z]
+    views = [c[:997] for c in coords]
+    b = bl.Bunch(views, g)
+    bl.bl_surrogate_apply(sur, b)
+    torch.cuda.synchronize()
+    for c, orig in zip(coords, z):
+        assert np.array_equal(c[997:].cpu().numpy().astype(np.float64), orig[997:])
+    first = [c[:997].cpu().numpy().copy() for c in coords]
+    coords2 = [torch.tensor(c, dtype=torch.float32, device="cuda") for c in z]
+    b2 = bl.Bunch([c[:997] for c in coords2], g)
+    bl.bl_surrogate_apply(sur, b2)
+    torch.cuda.synchronize()
+    for a, c in zip(first, coords2):
+        assert np.array_equal(a, c[:997].cpu().numpy())
+
+
+def _pairs(n, seed):
+    rng = np.random.default_rng(seed)
+    zin, g = _bunch(n, seed)
+    A = rng.normal(size=(6, 6)) * 0.3 + np.eye(6)
+    Zi = np.stack(zin)
+    sd = Zi.std(axis=1, keepdims=True)
+    Zo = (A @ (Zi / sd)) * sd + 0.1 * np.sin(Zi / sd) * sd
+    return Zi.astype(np.float32), Zo.astype(np.float32)
+
+
+def test_gradient_matches_oracle():
+    import torch
+    from paper_2402_17248_gb300 import bl
+    Zi, Zo = _pairs(1200, 11)
+    mu_i, sd_i = Zi.mean(axis=1), Zi.std(axis=1)
+    mu_o, sd_o = Zo.mean(axis=1), Zo.std(axis=1)
+    Ws, bs = mlp_init(WIDTHS, 2)
+    sur = bl.Surrogate(Ws, bs, mu_i, sd_i, mu_o, sd_o)
+    din = torch.tensor(Zi, device="cuda")
+    dout = torch.tensor(Zo, device="cuda")
+    grad = torch.zeros(bl.BL_MLP_NPARAM, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    bl.bl_surrogate_grad(sur, din, dout, grad, loss_out=loss)
+    torch.cuda.synchronize()
+    osur = _oracle_surrogate(Ws, bs, mu_i, sd_i, mu_o, sd_o)
+    X = (Zi.T.astype(np.float64) - mu_i) / sd_i
+    Y = (Zo.T.astype(np.float64) - mu_o) / sd_o
+    P, cache = mlp.forward(osur.Ws, osur.bs, X, bf16=True, keep=True)
+    L = mlp.mse(P, Y)
+    _, dW, db = mlp.backward(osur.Ws, cache, mlp.mse_grad(P, Y))
+    flat = []
+    for l in range(5):
+        flat += [dW[l].ravel(), db[l].ravel()]
+    flat = np.concatenate(flat)
+    g = grad.cpu().numpy().astype(np.float64)
+    rel = np.linalg.norm(g - flat) / np.linalg.norm(flat)
+    print("loss gpu %.6e oracle %.6e; gradient normwise rel err %.3e" % (loss.item(), L, rel))
+    assert abs(loss.item() / L - 1) < 1e-3
+    assert rel < 1e-2
+
+
+def test_training_reduces_loss_and_adam_step():
+    import torch
+    from paper_2402_17248_gb300 import bl
+    Zi, Zo = _pairs(24000, 12)
+    mu_i, sd_i = Zi.mean(axis=1), Zi.std(axis=1)
+    mu_o, sd_o = Zo.mean(axis=1), Zo.std(axis=1)
+    Ws, bs = mlp_init(WIDTHS, 3)
+    sur = bl.Surrogate(Ws, bs, mu_i, sd_i, mu_o, sd_o)
+    din = torch.tensor(Zi, device="cuda")
+    dout = torch.tensor(Zo, device="cuda")
+    # first Adam step moves every parameter by lr * sign(g) (bias-corrected)
+    grad = torch.zeros(bl.BL_MLP_NPARAM, device="cuda")
+    idx = torch.arange(0, 1200, device="cuda", dtype=torch.int64)
+    bl.bl_surrogate_grad(sur, din, dout, grad, idx=idx)
+    bl.bl_surrogate_train_step(sur, din, dout, idx=idx, lr=1e-3)
+    torch.cuda.synchronize()
+    W1, b1 = sur.params()
+    g = grad.cpu().numpy()
+    moved = np.concatenate([(W1[l] - np.asarray(Ws[l], np.float32)).ravel().astype(np.float64)
+                            for l in range(5)])
+    gw = np.concatenate([g[o:o + WIDTHS[l] * WIDTHS[l + 1]] for l, o in
+                         enumerate([0, 896, 17408, 33920, 50432])])
+    big = np.abs(gw) > 1e-5
+    assert np.allclose(moved[big], -1e-3 * np.sign(gw[big]), rtol=1e-3, atol=2e-7)
+    # a few hundred steps lower the held-out loss
+    loss = torch.zeros(1, device="cuda", dtype=torch.float64)
+    test_in, test_out = din[:, 20000:].contiguous(), dout[:, 20000:].contiguous()
+    bl.bl_surrogate_loss(sur, test_in, test_out, loss)
+    torch.cuda.synchronize()
+    l0 = loss.item()
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    for step in range(300):
+        idx = torch.randint(0, 20000, (1200,), device="cuda", generator=gen)
+        bl.bl_surrogate_train_step(sur, din, dout, idx=idx, lr=1e-3)
+    bl.bl_surrogate_loss(sur, test_in, test_out, loss)
+    torch.cuda.synchronize()
+    print("held-out loss %.4e -> %.4e" % (l0, loss.item()))
+    assert loss.item() < 0.2 * l0
