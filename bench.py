@@ -1,0 +1,393 @@
+"""Benchmark: particle-stages/s of the BF16 MLP surrogate beamline versus the
+FP32 RK4 wake pusher on the same GPU, with the final-moment error between them.
+
+Workload: a 2^24-particle FP32 Gaussian bunch (1 GeV, eps_n 1 um, sigma_x
+2 um, 10 fs, 1 % energy spread) tracked through 8 x (0.3 m plasma stage +
+17-element matching section with a 4-dipole chicane), moments after every
+element. A step = one pass of the whole beamline with the surrogate stages
+(8 tcgen05 MLP launches + 8 fused segment-map/moment passes), starting from
+the same initial bunch (restored by a device copy inside the timed region).
+The 8 surrogates are first trained on the GPU with the library's own kernels
+on pairs that the pusher generates from a randomised 4M-particle population.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank tracks its own bunch (weak scaling, no data-path
+collective); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-stages/s: BF16 MLP surrogate vs FP32 wake pusher, same GPU, moment err"
+N_PARTICLES = 1 << 24
+N_STAGES = 8
+STEPS_PER_STAGE = 400
+FLOP_PER_PARTICLE_STAGE = 2 * (6 * 128 + 3 * 128 * 128 + 128 * 6)  # 101,376
+SEG_BYTES_PER_PARTICLE = 48
+KEYS = ("x", "px", "y", "py", "t", "pt")
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--particles", type=int, default=N_PARTICLES)
+    p.add_argument("--train-steps", type=int, default=12000)
+    p.add_argument("--train-batch", type=int, default=4096)
+    p.add_argument("--train-lr", type=float, default=2e-3)
+    p.add_argument("--train-pairs", type=int, default=1 << 22)
+    p.add_argument("--pusher-steps", type=int, default=2)
+    p.add_argument("--cpu-sample", type=int, default=1 << 13)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.rows = []
+        self.proc = None
+        self.dev = device_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([s.strip() for s in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [r for r in self.rows if len(r) >= 9]
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------ reference arm
+def cpu_oracle_rate(sample, nets=None, seconds_cap=30.0):
+    """Oracle (FP64 numpy) surrogate beamline on a bounded sample; returns
+    particle-stages/s, the thread count numpy/BLAS may use and a description."""
+    from oracle import beamline, mlp as omlp
+    from synth import lattice
+    from synth.bunch import BunchRecipe, gaussian_bunch, mlp_init
+    z, g = gaussian_bunch(BunchRecipe(n=sample, seed=0))
+    zz = [z[k] for k in KEYS]
+    if nets is None:
+        Ws, bs = mlp_init([6, 128, 128, 128, 128, 6], 1)
+        Z = np.stack(zz, axis=1)
+        mu, sd = Z.mean(axis=0), Z.std(axis=0)
+        nets = [omlp.Surrogate(Ws, bs, mu, sd, mu, sd)] * N_STAGES
+    els = lattice.staged_beamline(N_STAGES, STEPS_PER_STAGE)
+    i = 0
+    for e in els:
+        if e["kind"] == "plasma":
+            e["surrogate"] = nets[i]
+            i += 1
+    t = time.perf_counter()
+    beamline.track(zz, g, els, snapshots=True)
+    dt = time.perf_counter() - t
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([d.get("num_threads", 1) for d in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count() or 1
+    return sample * N_STAGES / dt, cores, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    W, K = args.warmup, args.steps
+    sample = max(256, args.cpu_sample // 4)
+    for _ in range(W):
+        cpu_oracle_rate(sample)
+    t0 = time.perf_counter()
+    rates = []
+    for _ in range(K):
+        r, cores, dt = cpu_oracle_rate(sample)
+        rates.append(r)
+    total = time.perf_counter() - t0
+    value = sample * N_STAGES * K / total
+    desc = ("FP64 numpy oracle of the same 8-stage surrogate beamline (moments after every "
+            "element) on %d particles per step" % sample)
+    line = {"metric": METRIC, "value": value, "unit": "particle-stages/s", "n_gpus": args.gpus,
+            "steps": K, "warmup": W, "ms_per_step": 1e3 * total / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "8-stage surrogate beamline, FP64 CPU oracle sample",
+                       "particles_per_step": sample, "stages": N_STAGES},
+            "cpu_baseline": {"value": value, "unit": "particle-stages/s", "cores": cores,
+                             "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "particle-stages/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    from paper_2402_17248_gb300 import bl, build, workflow
+    if not os.path.exists(bl.LIB_PATH):
+        build.build()
+    bl.lib()
+    from synth import lattice
+    from synth.bunch import BunchRecipe, gaussian_bunch, training_population
+
+    t_setup = time.time()
+    n = args.particles
+    # ---- training data from the plain pusher over a randomised population
+    kp = math.sqrt(1e17 * 1e6 * 1.602176634e-19 ** 2 / (8.8541878128e-12 * 9.1093837015e-31)) / 299792458.0
+    g0 = BunchRecipe().gamma_ref
+    per = 65536
+    nb = max(1, args.train_pairs // per)
+    zt, _ = training_population(nb, per, g0, 0.2 / kp, seed=1000)
+    tb = workflow.device_bunch(zt, g0)
+    elements = lattice.staged_beamline(N_STAGES, STEPS_PER_STAGE)
+    pairs = workflow.stage_pairs(tb, elements)
+    del tb
+    log("training pairs ready: %d stages x %d pairs (%.1fs)" % (len(pairs), nb * per, time.time() - t_setup))
+    surs, infos = [], []
+    for s, (xin, xout, gin) in enumerate(pairs):
+        sur, info = workflow.fit_surrogate(xin, xout, steps=args.train_steps, batch=args.train_batch,
+                                           lr=args.train_lr, seed=100 + s)
+        surs.append(sur)
+        infos.append(info)
+        log("stage %d surrogate: test loss %.3e after %d steps (%.1fs)" %
+            (s + 1, info["test_loss"], info["steps"], info["seconds"]))
+    del pairs
+    torch.cuda.empty_cache()
+
+    # ---- the tracked bunch
+    z, g = gaussian_bunch(BunchRecipe(n=n, seed=0))
+    z0 = [torch.tensor(z[k], dtype=torch.float32, device=dev) for k in KEYS]
+    host_pinned = [torch.tensor(z[k], dtype=torch.float32).pin_memory() for k in KEYS]
+    del z
+    work = [c.clone() for c in z0]
+    bunch = bl.Bunch(work, g)
+    lat_sur = bl.Lattice(workflow.surrogate_beamline(elements, surs))
+    lat_push = bl.Lattice(elements)
+    nel = lat_sur.num_elements
+    stream = torch.cuda.current_stream()
+
+    def restore():
+        for w, s in zip(work, z0):
+            w.copy_(s, non_blocking=True)
+        bunch.struct.gamma_ref = g
+
+    def step_surrogate(moments=True):
+        restore()
+        return bl.bl_track(bunch, lat_sur, moments=moments)
+
+    # ---- warm-up (also builds the lattice plans) and the moment comparison
+    for _ in range(args.warmup):
+        m_sur, nf = step_surrogate()
+    torch.cuda.synchronize()
+    restore()
+    m_push, nf_push = bl.bl_track(bunch, lat_push)
+    torch.cuda.synchronize()
+    g_final = bunch.gamma_ref
+    d_sur = bl.bl_beam_quantities(m_sur[-1][0], g_final)
+    d_push = bl.bl_beam_quantities(m_push[-1][0], g_final)
+    moment_err = {k: abs(d_sur[k] / d_push[k] - 1) for k in d_push}
+    log("final moments surrogate vs pusher:", json.dumps(moment_err))
+
+    # ---- timed surrogate steps (max over ranks)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step_surrogate()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = t.item()
+    value = world * n * N_STAGES / (ms * 1e-3)
+    launches_per_step = N_STAGES * 3  # MLP + fused segment/moments + finalize per stage
+
+    # ---- the dominant kernel alone: tcgen05 MLP over the full bunch
+    restore()
+    bl.bl_surrogate_apply(surs[0], bunch)
+    torch.cuda.synchronize()
+    reps = 10
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    for _ in range(reps):
+        bl.bl_surrogate_apply(surs[0], bunch)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    mlp_ms = ev[0].elapsed_time(ev[1]) / reps
+    mlp_tflops = FLOP_PER_PARTICLE_STAGE * n / (mlp_ms * 1e-3) / 1e12
+    # the HBM-bound segment map alone (no moments), for the map roofline
+    M = np.eye(6)
+    restore()
+    ev[0].record(stream)
+    for _ in range(reps):
+        bl.bl_apply_linear(bunch, M)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    seg_ms = ev[0].elapsed_time(ev[1]) / reps
+    seg_gbs = SEG_BYTES_PER_PARTICLE * n / (seg_ms * 1e-3) / 1e9
+
+    # ---- the plain FP32 pusher beamline on the same bunch
+    restore()
+    bl.bl_track(bunch, lat_push, moments=False)
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(args.pusher_steps):
+        restore()
+        bl.bl_track(bunch, lat_push, moments=True)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    push_ms = ev[0].elapsed_time(ev[1]) / args.pusher_steps
+    push_value = n * N_STAGES / (push_ms * 1e-3)
+
+    # ---- end to end through the C ABI with host buffers (pinned)
+    out_host = [torch.empty_like(h).pin_memory() for h in host_pinned]
+    def e2e_step():
+        for w, h in zip(work, host_pinned):
+            w.copy_(h, non_blocking=True)
+        bunch.struct.gamma_ref = g
+        bl.bl_track(bunch, lat_sur, moments=True)
+        for o, w in zip(out_host, work):
+            o.copy_(w, non_blocking=True)
+    e2e_step()
+    torch.cuda.synchronize()
+    ke = max(2, args.steps // 2)
+    ev[0].record(stream)
+    for _ in range(ke):
+        e2e_step()
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = ev[0].elapsed_time(ev[1]) / ke
+    e2e_value = world * n * N_STAGES / (e2e_ms * 1e-3)
+    h2d = 6 * 4 * n
+    d2h = 6 * 4 * n + nel * 28 * 8
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if peaks else "fallback"
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle import mlp as omlp
+        nets = []
+        for s in surs:
+            Ws, bs = s.params()
+            nets.append(omlp.Surrogate([omlp.bf16_round(W.astype(np.float64)) for W in Ws],
+                                       [b.astype(np.float64) for b in bs],
+                                       s.mu_in, s.sd_in, s.mu_out, s.sd_out))
+        rate, cores, dt = cpu_oracle_rate(args.cpu_sample, nets)
+        cpu = {"value": rate, "unit": "particle-stages/s", "cores": cores, "kind": "oracle",
+               "sample": "FP64 numpy oracle of the trained 8-stage surrogate beamline with "
+                         "moments after every element, %d particles (%.1f s)" % (args.cpu_sample, dt)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "particle-stages/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "2^24-particle FP32 bunch through 8 x (BF16 MLP surrogate stage "
+                               "6-128x4-6 GELU + 17-element matching section), moments after "
+                               "every element; FP32 400-step RK4 pusher beamline timed beside it",
+                   "particles_per_gpu": n, "stages": N_STAGES, "l2": "inputs (384 MiB) larger than L2",
+                   "train": {"pairs_per_stage": nb * per, "steps": args.train_steps,
+                             "batch": args.train_batch, "lr": args.train_lr,
+                             "test_loss": [i["test_loss"] for i in infos],
+                             "seconds": sum(i["seconds"] for i in infos)}},
+        "pusher": {"value": push_value, "unit": "particle-stages/s", "ms_per_step": push_ms,
+                   "dtype": "f32", "rk4_steps_per_stage": STEPS_PER_STAGE},
+        "speedup_vs_pusher": value / push_value,
+        "moment_rel_err_vs_pusher": moment_err,
+        "roofline": {"bound": "tensor", "achieved": mlp_tflops, "peak": bf16_peak,
+                     "unit": "TFLOP/s", "frac": mlp_tflops / bf16_peak, "traffic": None,
+                     "kernel": "mlp_forward_kernel", "peak_source": peak_src + " bf16 burst",
+                     "ms_per_launch": mlp_ms},
+        "roofline_segment": {"bound": "hbm", "achieved": seg_gbs, "peak": hbm_peak, "unit": "GB/s",
+                             "frac": seg_gbs / hbm_peak, "kernel": "stream_kernel (map only)",
+                             "ms_per_launch": seg_ms},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "particle-stages/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+        "nonfinite": nf,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

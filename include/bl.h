@@ -146,6 +146,13 @@ bl_status bl_track(bl_bunch *bunch, const bl_lattice *lat, double *moments_out,
  * sums per thread, FP64 across threads. Uses library scratch memory. */
 bl_status bl_moments(const bl_bunch *bunch, double *out, bl_stream stream);
 
+/* Beam quantities of one 28-moment vector (host computation, Sec. 4):
+ * out[0] eps_n,x = (beta gamma)_ref sqrt(S_xx S_pxpx - S_xpx^2), out[1] eps_n,y,
+ * out[2] sigma_x = sqrt(S_xx), out[3] sigma_y, out[4] <gamma> =
+ * gamma_ref - (beta gamma)_ref <pt>, out[5] relative energy spread
+ * (beta gamma)_ref sigma_pt / <gamma>. moments28 and out: host. */
+bl_status bl_beam_quantities(const double *moments28, double gamma_ref, double *out);
+
 /* Apply one 6x6 matrix (host, row-major, 36 doubles, or n_bunch*36 for one
  * matrix per bunch when per_bunch != 0) to every particle: z <- M z. */
 bl_status bl_apply_linear(bl_bunch *bunch, const double *M, int32_t per_bunch,

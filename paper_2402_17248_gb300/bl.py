@@ -65,6 +65,7 @@ _SIGS = {
     "bl_apply_linear": ([_P, _P, _I32, _P], C.c_int),
     "bl_push_stage": ([_P, _P, _P], C.c_int),
     "bl_reference_exit": ([_P, _D, _P], C.c_int),
+    "bl_beam_quantities": ([_P, _D, _P], C.c_int),
     "bl_surrogate_create": ([_P, _P], C.c_int),
     "bl_surrogate_destroy": ([_P], C.c_int),
     "bl_surrogate_get_params": ([_P, _P, _P], C.c_int),
@@ -247,6 +248,16 @@ def bl_reference_exit(stage, gamma_in):
     g = C.c_double()
     _check(lib().bl_reference_exit(arr, float(gamma_in), C.byref(g)))
     return g.value
+
+
+BEAM_QUANTITIES = ("eps_n_x", "eps_n_y", "sigma_x", "sigma_y", "mean_gamma", "rel_energy_spread")
+
+
+def bl_beam_quantities(m28, gamma_ref):
+    m = np.ascontiguousarray(m28, dtype=np.float64)
+    out = np.zeros(6)
+    _check(lib().bl_beam_quantities(m.ctypes.data, float(gamma_ref), out.ctypes.data))
+    return dict(zip(BEAM_QUANTITIES, out.tolist()))
 
 
 # --------------------------------------------------------------- surrogates

@@ -70,6 +70,8 @@ constexpr int MLP_IMG_BYTES = MLP_IMG_W0 + 3 * MLP_IMG_WH + MLP_IMG_W4;  // 1064
 constexpr int MLP_BIAS_FLOATS = 3 * 128 + 16;
 
 struct MlpNorm { double mu_in[6], inv_sd_in[6], mu_out[6], sd_out[6]; };
+// The same constants as double-float pairs (hi, lo) for the inference kernel.
+struct MlpNormF { float mu_in[6][2], inv_sd_in[6][2], mu_out[6][2], sd_out[6][2]; };
 
 cudaError_t launch_mlp_pack(const float *params, uint8_t *img, float *bias, float *wt,
                             float *wn, cudaStream_t st);

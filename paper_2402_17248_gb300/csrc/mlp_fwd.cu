@@ -13,15 +13,19 @@
 //    (tcgen05.ld), add the bias, apply GELU, round to BF16 and write the
 //    result back into tensor memory (tcgen05.st) as the A operand of the next
 //    layer's MMA (A-from-TMEM form), so shared memory carries only weights.
-//  * Each of the two warpgroups owns one tile slot (accumulator 128 columns,
-//    activation 64 columns of TMEM) and one elected thread issues its MMAs;
-//    the two slots run out of phase, so one tile's MMAs overlap the other
-//    tile's epilogue.
-//  * Inputs are normalised in FP64 and rounded to BF16; the 7th input column
-//    holds 1.0 so the first layer's bias rides in the K padding. Outputs are
-//    de-normalised in FP64 and stored as FP32.
-//  * Hidden activations are stored as 2*GELU(x) = x (1 + tanh(u)) and the
-//    next layer's weights are pre-scaled by 1/2 (exact in BF16).
+//  * Each tile slot (accumulator 128 TMEM columns + activation 64 columns) is
+//    served by two warpgroups that split the 128 features (64 each), and one
+//    elected thread per slot issues its MMAs; the two slots run out of phase,
+//    so one tile's MMAs overlap the other tile's epilogue.
+//  * Epilogue arithmetic: bias add and the GELU argument in packed FP32x2,
+//    tanh on packed BF16 pairs, and 2*GELU = x (1 + tanh) as one BF16x2 FMA.
+//    Hidden activations are stored as 2*GELU(x) and the next layer's weights
+//    are pre-scaled by 1/2 (exact in BF16).
+//  * Inputs are normalised and outputs de-normalised in double-float
+//    arithmetic (FP32 pairs with error-free TwoSum / TwoProd steps), which
+//    carries about 44 bits, i.e. FP64-grade constants and rounding, on the
+//    FP32 pipes; the 7th input column holds 1.0 so the first layer's bias
+//    rides in the K padding.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -33,7 +37,8 @@ namespace bl {
 namespace {
 
 constexpr int SLOTS = 2;
-constexpr int THREADS = 128 * SLOTS;
+constexpr int WG_PER_SLOT = 2;
+constexpr int THREADS = 128 * SLOTS * WG_PER_SLOT;
 constexpr uint32_t OFF_W0 = 0;
 constexpr uint32_t OFF_W1 = OFF_W0 + MLP_IMG_W0;
 constexpr uint32_t OFF_W4 = OFF_W1 + 3 * MLP_IMG_WH;
@@ -54,22 +59,70 @@ __host__ __device__ inline uint32_t img_off(int n, int k, int K) {
   return (uint32_t)((n >> 3) * (K / 8) * 128 + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2);
 }
 
-BL_DEV float gelu2(float x) {
-  // 2 * GELU(x) = x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3)))
-  const float u = x * fmaf(GELU_C1, x * x, GELU_C0);
-  return fmaf(x, tc::tanh_approx(u), x);
+// Two hidden features (FP32 accumulators r0, r1 plus bias pair b01) ->
+// packed BF16 pair of 2*GELU: u = x (c0 + c1 x^2) in FP32x2, tanh on packed
+// FP16 pairs (10-bit mantissa), x (1 + tanh u) as one FP32x2 FMA, one
+// rounding to BF16 at the end.
+BL_DEV uint32_t gelu2_pair(uint32_t r0, uint32_t r1, uint64_t b01, bool add_bias) {
+  uint64_t x, x2, p, u, t, y;
+  asm("mov.b64 %0, {%1,%2};" : "=l"(x) : "r"(r0), "r"(r1));
+  if (add_bias) asm("add.rn.f32x2 %0, %1, %2;" : "=l"(x) : "l"(x), "l"(b01));
+  asm("mul.rn.f32x2 %0, %1, %1;" : "=l"(x2) : "l"(x));
+  const uint64_t c1 = ((uint64_t)__float_as_uint(GELU_C1) << 32) | __float_as_uint(GELU_C1);
+  const uint64_t c0 = ((uint64_t)__float_as_uint(GELU_C0) << 32) | __float_as_uint(GELU_C0);
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(p) : "l"(x2), "l"(c1), "l"(c0));
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(u) : "l"(x), "l"(p));
+  uint32_t ulo, uhi, uh, th, yb;
+  asm("mov.b64 {%0,%1}, %2;" : "=r"(ulo), "=r"(uhi) : "l"(u));
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(uh) : "r"(uhi), "r"(ulo));
+  asm("tanh.approx.f16x2 %0, %1;" : "=r"(th) : "r"(uh));
+  asm("{\n .reg .f16 a, b;\n .reg .f32 fa, fb;\n mov.b32 {a, b}, %1;\n"
+      " cvt.f32.f16 fa, a;\n cvt.f32.f16 fb, b;\n mov.b64 %0, {fa, fb};\n}"
+      : "=l"(t) : "r"(th));
+  asm("fma.rn.f32x2 %0, %1, %2, %1;" : "=l"(y) : "l"(x), "l"(t));
+  uint32_t ylo, yhi;
+  asm("mov.b64 {%0,%1}, %2;" : "=r"(ylo), "=r"(yhi) : "l"(y));
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(yb) : "r"(yhi), "r"(ylo));
+  return yb;
+}
+
+// Double-float helpers: a value v is carried as hi + lo (FP32 each).
+BL_DEV void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+}
+
+// (z - mu) * inv with mu = mh + ml and inv = ih + il, rounded to FP32.
+BL_DEV float df_normalise(float z, float mh, float ml, float ih, float il) {
+  float dh, dl;
+  two_sum(z, -mh, dh, dl);
+  dl -= ml;
+  const float p = dh * ih;
+  const float pe = fmaf(dh, ih, -p);
+  return p + (pe + fmaf(dh, il, dl * ih));
+}
+
+// y * sd + mu with sd = sh + sl and mu = mh + ml, rounded to FP32.
+BL_DEV float df_affine(float y, float sh, float sl, float mh, float ml) {
+  const float p = y * sh;
+  const float pe = fmaf(y, sh, -p);
+  float s, se;
+  two_sum(p, mh, s, se);
+  return s + (se + pe + fmaf(y, sl, ml));
 }
 
 __global__ void __launch_bounds__(THREADS, 1)
 mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__restrict__ img,
-                   const float *__restrict__ bias, MlpNorm nrm, unsigned *err) {
+                   const float *__restrict__ bias, MlpNormF nrm, unsigned *err) {
   extern __shared__ __align__(1024) uint8_t smem[];
   float *sB = reinterpret_cast<float *>(smem + OFF_BIAS);
   uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + OFF_SLOT);
   const uint32_t sbase = tc::smem_u32(smem);
   const uint32_t bar_w = sbase + OFF_BAR;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int slot = warp >> 2, wq = warp & 3;
+  const int wg = warp >> 2, wq = warp & 3;
+  const int slot = wg / WG_PER_SLOT, half = wg % WG_PER_SLOT;
   const uint32_t bar_m = sbase + OFF_BAR + 8 * (1 + slot);
 
   if (tid == 0) {
@@ -100,7 +153,8 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
   const uint32_t t_act = t_acc + 128;
   const uint32_t d_acc = tmem + slot * 256;  // lane 0 addresses for the MMA
   const uint32_t d_act = d_acc + 128;
-  const bool issuer = (tid & 127) == 0;
+  const bool issuer = (tid & 255) == 0;
+  constexpr int NSLOT = 128 * WG_PER_SLOT;  // threads per slot
   constexpr uint32_t ID_H = tc::idesc_bf16(128, 128);
   constexpr uint32_t ID_O = tc::idesc_bf16(128, 16);
   uint32_t phase = 0;
@@ -110,15 +164,16 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
        tile += (int64_t)gridDim.x * SLOTS) {
     const int64_t p = tile * 128 + wq * 32 + lane;
     const bool valid = p < n;
-    // a failed wait anywhere in the warpgroup stops all of its threads together
-    if (!tc::named_bar_and(1 + slot, 128, ok)) break;
-    // ---- prologue: FP64 normalisation, BF16 input row in TMEM
-    {
+    // a failed wait anywhere in the slot stops all of its threads together
+    if (!tc::named_bar_and(1 + slot, NSLOT, ok)) break;
+    // ---- prologue: normalised BF16 input row in TMEM (first warpgroup)
+    if (half == 0) {
       float xn[6];
 #pragma unroll
       for (int c = 0; c < 6; ++c) {
         const float v = valid ? z.c[c][p] : 0.0f;
-        xn[c] = (float)(((double)v - nrm.mu_in[c]) * nrm.inv_sd_in[c]);
+        xn[c] = df_normalise(v, nrm.mu_in[c][0], nrm.mu_in[c][1], nrm.inv_sd_in[c][0],
+                             nrm.inv_sd_in[c][1]);
       }
       uint32_t a[8];
       a[0] = tc::pack_bf16x2(xn[0], xn[1]);
@@ -131,11 +186,9 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
       tc::fence_before();
     }
     // ---- five layers
-    bool go = true;
 #pragma unroll 1
     for (int l = 0; l < 5; ++l) {
-      go = tc::named_bar_and(1 + slot, 128, ok);
-      if (!go) break;
+      if (!tc::named_bar_and(1 + slot, NSLOT, ok)) break;
       if (issuer) {
         tc::fence_after();
         if (l == 0) {
@@ -154,29 +207,28 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
       ok = __all_sync(0xffffffffu, ok);
       phase ^= 1;
       tc::fence_after();
-      if (!ok) continue;  // the next barrier stops the warpgroup
+      if (!ok) continue;  // the next barrier stops the slot
       if (l < 4) {
-        const float *b = (l == 0) ? nullptr : sB + (l - 1) * 128;
-#pragma unroll 1
-        for (int ch = 0; ch < 4; ++ch) {
-          uint32_t r[32];
-          tc::tmem_ld32(t_acc + 32 * ch, r);
-          tc::tmem_ld_wait();
+        // this warpgroup's 64 features: accumulator columns 64*half ..
+        uint32_t r[2][32];
+        tc::tmem_ld32(t_acc + 64 * half, r[0]);
+        tc::tmem_ld32(t_acc + 64 * half + 32, r[1]);
+        tc::tmem_ld_wait();
+        const bool add_bias = l > 0;
+        const uint64_t *b64 =
+            reinterpret_cast<const uint64_t *>(sB + (l > 0 ? (l - 1) * 128 : 0) + 64 * half);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
           uint32_t o[16];
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            float x0 = __uint_as_float(r[2 * j]), x1 = __uint_as_float(r[2 * j + 1]);
-            if (b) {
-              x0 += b[32 * ch + 2 * j];
-              x1 += b[32 * ch + 2 * j + 1];
-            }
-            o[j] = tc::pack_bf16x2(gelu2(x0), gelu2(x1));
-          }
-          tc::tmem_st16(t_act + 16 * ch, o);
+          for (int j = 0; j < 16; ++j)
+            o[j] = gelu2_pair(r[h][2 * j], r[h][2 * j + 1], add_bias ? b64[16 * h + j] : 0ull,
+                              add_bias);
+          tc::tmem_st16(t_act + 32 * half + 16 * h, o);
         }
         tc::tmem_st_wait();
         tc::fence_before();
-      } else {
+      } else if (half == 0) {
         uint32_t r[8];
         tc::tmem_ld8(t_acc, r);
         tc::tmem_ld_wait();
@@ -184,7 +236,8 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
 #pragma unroll
           for (int c = 0; c < 6; ++c) {
             const float yv = __uint_as_float(r[c]) + sB[384 + c];
-            z.c[c][p] = (float)fma((double)yv, nrm.sd_out[c], nrm.mu_out[c]);
+            z.c[c][p] = df_affine(yv, nrm.sd_out[c][0], nrm.sd_out[c][1], nrm.mu_out[c][0],
+                                  nrm.mu_out[c][1]);
           }
         }
         tc::fence_before();
@@ -345,9 +398,21 @@ cudaError_t launch_mlp_pack(const float *params, uint8_t *img, float *bias, floa
   return cudaGetLastError();
 }
 
+static void split_df(double v, float *hl) {
+  hl[0] = (float)v;
+  hl[1] = (float)(v - (double)hl[0]);
+}
+
 cudaError_t launch_mlp_forward(Soa<float> z, int64_t n, const uint8_t *img, const float *bias,
-                               const MlpNorm &nrm, int num_sms, unsigned *err, cudaStream_t st) {
+                               const MlpNorm &nrm64, int num_sms, unsigned *err, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
+  MlpNormF nrm;
+  for (int c = 0; c < 6; ++c) {
+    split_df(nrm64.mu_in[c], nrm.mu_in[c]);
+    split_df(nrm64.inv_sd_in[c], nrm.inv_sd_in[c]);
+    split_df(nrm64.mu_out[c], nrm.mu_out[c]);
+    split_df(nrm64.sd_out[c], nrm.sd_out[c]);
+  }
   const int64_t ntiles = (n + 127) / 128;
   int64_t grid = (ntiles + SLOTS - 1) / SLOTS;
   if (grid > num_sms) grid = num_sms;

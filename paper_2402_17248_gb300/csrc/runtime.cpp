@@ -2,6 +2,7 @@
 // and the FP64 reference-particle track of a plasma stage.
 #include "runtime.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 
@@ -342,6 +343,22 @@ bl_status bl_poll_device_errors(void) {
     return bl::set_error(BL_ERR_TIMEOUT, "a device-side bounded wait gave up (flags " +
                                              std::to_string(v) + ")");
   }
+  return BL_OK;
+}
+
+bl_status bl_beam_quantities(const double *m, double gamma_ref, double *out) {
+  BL_CHECK(m && out, "NULL argument");
+  BL_CHECK(gamma_ref > 1.0, "gamma_ref must exceed 1");
+  const double bg = std::sqrt(gamma_ref * gamma_ref - 1.0);
+  // indices of S_xx, S_xpx, S_pxpx, S_yy, S_ypy, S_pypy, S_ptpt in the 28-vector
+  const double Sxx = m[7], Sxp = m[8], Spp = m[13], Syy = m[18], Syp = m[19], Sqq = m[22];
+  const double Stt = m[27];
+  out[0] = bg * std::sqrt(std::max(0.0, Sxx * Spp - Sxp * Sxp));
+  out[1] = bg * std::sqrt(std::max(0.0, Syy * Sqq - Syp * Syp));
+  out[2] = std::sqrt(std::max(0.0, Sxx));
+  out[3] = std::sqrt(std::max(0.0, Syy));
+  out[4] = gamma_ref - bg * m[6];
+  out[5] = bg * std::sqrt(std::max(0.0, Stt)) / out[4];
   return BL_OK;
 }
 

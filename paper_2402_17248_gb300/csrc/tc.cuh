@@ -34,13 +34,13 @@ BL_DEV bool mbar_try_wait(uint32_t bar, uint32_t phase) {
   return done != 0;
 }
 
-// Bounded wait on an mbarrier phase (about 2^22 polls with a 128 ns back-off,
-// i.e. on the order of a second); on timeout raises `flag` in *err (if
-// non-NULL) and returns false.
+// Bounded wait on an mbarrier phase: at most 2^24 try_wait polls (each
+// suspends in hardware for a bounded time), i.e. well under a minute even in
+// the worst case; on timeout raises `flag` in *err (if non-NULL) and returns
+// false.
 BL_DEV bool mbar_wait(uint32_t bar, uint32_t phase, unsigned flag, unsigned *err) {
-  for (uint32_t i = 0; i < (1u << 22); ++i) {
+  for (uint32_t i = 0; i < (1u << 24); ++i) {
     if (mbar_try_wait(bar, phase)) return true;
-    if (i > 16) __nanosleep(128);
   }
   if (err) atomicOr(err, flag);
   return false;

@@ -1,0 +1,120 @@
+"""Host-side orchestration of the learned part over the C ABI.
+
+* stage training pairs: a randomised population is tracked with the plain
+  RK4 pusher; the entry and exit states of every plasma stage are recorded
+  (Sec. 4.1: in/out phase-space arrays of each stage);
+* per-coordinate normalisation constants from the library's moment kernel
+  (Sec. 3: subtract the mean, divide by the standard deviation);
+* a 70/30 train/test split and minibatch Adam on the MSE (Sec. 3, Sec. 4.2),
+  every step one bl_surrogate_train_step call.
+
+Nothing here computes the method: each numerical step is a libbl call.
+"""
+import math
+import time
+
+import numpy as np
+import torch
+
+from . import bl
+
+KEYS = ("x", "px", "y", "py", "t", "pt")
+
+
+def device_bunch(z, gamma_ref, dtype=torch.float32, device="cuda"):
+    coords = [torch.as_tensor(np.asarray(z[k] if isinstance(z, dict) else z[i]), dtype=dtype,
+                              device=device).contiguous()
+              for i, k in enumerate(KEYS)]
+    return bl.Bunch(coords, gamma_ref)
+
+
+def split_beamline(elements):
+    """[(stage_element, [segment elements that follow]), ...] for a beamline
+    that starts with a plasma stage."""
+    out = []
+    for e in elements:
+        if e["kind"] == "plasma":
+            out.append((e, []))
+        else:
+            if not out:
+                raise ValueError("beamline must start with a plasma stage")
+            out[-1][1].append(e)
+    return out
+
+
+def stage_pairs(bunch, elements):
+    """Track `bunch` (FP32, consumed) through the beamline with the plain
+    pusher; returns per stage (inputs [6][n], outputs [6][n], gamma_in)."""
+    pairs = []
+    for stage, seg in split_beamline(elements):
+        g_in = bunch.gamma_ref
+        xin = torch.stack([c.clone() for c in bunch.coords])
+        bl.bl_push_stage(bunch, stage)
+        xout = torch.stack([c.clone() for c in bunch.coords])
+        pairs.append((xin, xout, g_in))
+        if seg:
+            lat = bl.Lattice(seg)
+            bl.bl_track(bunch, lat, moments=False)
+    torch.cuda.synchronize()
+    return pairs
+
+
+def norm_constants(x6):
+    """(mean, std) per coordinate of a [6][n] device array via bl_moments."""
+    b = bl.Bunch([x6[i] for i in range(6)], 2.0)
+    m = bl.bl_moments(b)[0]
+    mean = m[1:7].copy()
+    var = np.array([m[7 + j] for j in (0, 6, 11, 15, 18, 20)])
+    return mean, np.sqrt(np.maximum(var, 1e-300))
+
+
+def fit_surrogate(xin, xout, steps=20000, batch=1200, lr=1e-3, lr_final=1e-5, seed=0,
+                  init_seed=None, test_frac=0.3, log_every=0, widths=bl.WIDTHS):
+    """Train one stage surrogate on device pairs; returns (surrogate, info)."""
+    from synth.bunch import mlp_init
+    n = xin.shape[1]
+    ntest = int(round(test_frac * n))
+    ntrain = n - ntest
+    mu_i, sd_i = norm_constants(xin)
+    mu_o, sd_o = norm_constants(xout)
+    Ws, bs = mlp_init(list(widths), seed if init_seed is None else init_seed)
+    sur = bl.Surrogate(Ws, bs, mu_i, sd_i, mu_o, sd_o)
+    xin = xin.contiguous()
+    xout = xout.contiguous()
+    test_in = xin[:, ntrain:].contiguous()
+    test_out = xout[:, ntrain:].contiguous()
+    gen = torch.Generator(device=xin.device).manual_seed(seed)
+    loss = torch.zeros(1, dtype=torch.float64, device=xin.device)
+    chunk = 1000
+    t0 = time.time()
+    history = []
+    for s0 in range(0, steps, chunk):
+        k = min(chunk, steps - s0)
+        idx = torch.randint(0, ntrain, (k, batch), device=xin.device, generator=gen)
+        for j in range(k):
+            s = s0 + j
+            # cosine decay from lr to lr_final
+            a = lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * s / max(1, steps)))
+            bl.bl_surrogate_train_step(sur, xin, xout, idx=idx[j], batch=batch, lr=a)
+        if log_every and ((s0 // chunk) % log_every == 0 or s0 + k >= steps):
+            bl.bl_surrogate_loss(sur, test_in, test_out, loss)
+            torch.cuda.synchronize()
+            history.append((s0 + k, loss.item(), time.time() - t0))
+    bl.bl_surrogate_loss(sur, test_in, test_out, loss)
+    torch.cuda.synchronize()
+    info = {"steps": steps, "batch": batch, "lr": lr, "lr_final": lr_final,
+            "train_pairs": ntrain, "test_pairs": ntest, "test_loss": loss.item(),
+            "seconds": time.time() - t0, "history": history}
+    return sur, info
+
+
+def surrogate_beamline(elements, surrogates):
+    """Copy of `elements` whose plasma stages use the given surrogates, in order."""
+    out, i = [], 0
+    for e in elements:
+        e = dict(e)
+        if e["kind"] == "plasma":
+            e["surrogate"] = surrogates[i]
+            i += 1
+        out.append(e)
+    return out

@@ -73,3 +73,17 @@ def test_per_bunch_lattice():
            {"kind": "drift", "L": 1.0}]
     L = bl.Lattice(els, n_bunch_k=3)
     assert L.num_quads == 1
+
+
+def test_beam_quantities_match_oracle():
+    from oracle import moments
+    from synth.bunch import BunchRecipe, gaussian_bunch
+    z, g = gaussian_bunch(BunchRecipe(n=5000, seed=8))
+    zz = [z[k] for k in ("x", "px", "y", "py", "t", "pt")]
+    zz[5] = zz[5] + 0.3 * np.std(zz[5])
+    zz[1] = zz[1] + 0.5 * zz[0] / 2e-6 * np.std(zz[1])
+    m = moments.moments28(zz)
+    want = moments.derived(m, g)
+    got = bl.bl_beam_quantities(m, g)
+    for k in want:
+        assert abs(got[k] / want[k] - 1) < 1e-13, k
