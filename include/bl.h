@@ -146,6 +146,30 @@ bl_status bl_track(bl_bunch *bunch, const bl_lattice *lat, double *moments_out,
  * sums per thread, FP64 across threads. Uses library scratch memory. */
 bl_status bl_moments(const bl_bunch *bunch, double *out, bl_stream stream);
 
+/* Size of the fixed scratch used by bl_moments_noalloc, in partial-sum
+ * slots of 28 doubles (about 7.3 MB): one slot per 4096-particle block plus
+ * one per bunch, so one call handles up to about (32768 - n_bunch) * 4096
+ * particles. */
+#define BL_NOALLOC_SCRATCH_SLOTS 32768
+
+/* bl_moments without any device allocation by the library, for callers that
+ * cannot allocate device memory: a framework whose caching allocator owns the
+ * GPU's memory, real-time or embedded code that reserves all memory up front,
+ * or a pipeline that cannot tolerate the device-wide synchronisation that
+ * cudaMalloc/cudaFree may imply. The paper has no counterpart.
+ * Results are those of bl_moments. out: device-accessible memory (device,
+ * managed or mapped pinned host), n_bunch * 28 doubles, valid after the
+ * stream is synchronised. The per-block partial sums live in one fixed device
+ * array of BL_NOALLOC_SCRATCH_SLOTS slots that the library defines at file
+ * scope; every GPU that loads the library keeps it until the process exits.
+ * Inputs larger than that scratch are rejected with BL_ERR_INVALID_ARG.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * All calls share the one array and every call overwrites what it reads, so
+ * no state carries over from call to call; calls whose work overlaps on the
+ * GPU (different streams or threads at the same time) race on it. */
+bl_status bl_moments_noalloc(const bl_bunch *bunch, double *out, bl_stream stream);
+
 /* Beam quantities of one 28-moment vector (host computation, Sec. 4):
  * out[0] eps_n,x = (beta gamma)_ref sqrt(S_xx S_pxpx - S_xpx^2), out[1] eps_n,y,
  * out[2] sigma_x = sqrt(S_xx), out[3] sigma_y, out[4] <gamma> =

@@ -62,6 +62,7 @@ _SIGS = {
     "bl_lattice_num_quads": ([_P], C.c_int32),
     "bl_track": ([_P, _P, _P, _P, _P], C.c_int),
     "bl_moments": ([_P, _P, _P], C.c_int),
+    "bl_moments_noalloc": ([_P, _P, _P], C.c_int),
     "bl_apply_linear": ([_P, _P, _I32, _P], C.c_int),
     "bl_push_stage": ([_P, _P, _P], C.c_int),
     "bl_reference_exit": ([_P, _D, _P], C.c_int),
@@ -229,6 +230,12 @@ def bl_moments(bunch, out=None, stream=None):
     _check(lib().bl_moments(bunch.ref(), h.ctypes.data, _stream(stream)))
     torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
     return h
+
+
+def bl_moments_noalloc(bunch, out, stream=None):
+    """Moments into `out` (device float64 tensor of n_bunch*28) using the
+    library's fixed scratch array instead of any allocation."""
+    _check(lib().bl_moments_noalloc(bunch.ref(), _ptr(out), _stream(stream)))
 
 
 def bl_apply_linear(bunch, M, stream=None):
