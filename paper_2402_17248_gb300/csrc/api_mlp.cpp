@@ -150,7 +150,7 @@ bl_status bl_surrogate_apply(const bl_surrogate *s, bl_bunch *b, bl_stream strea
     BL_CUDA(mlp_forward_configure());
     ctx->mlp_configured = true;
   }
-  BL_CUDA(launch_mlp_forward(soa_of<float>(b), b->n, s->img, s->bias, s->nrm, ctx->num_sms,
+  BL_CUDA(launch_mlp_forward(soa_of<float>(b), b->n, s->img, s->nrm, ctx->num_sms,
                              ctx->err_word, (cudaStream_t)stream));
   return BL_OK;
 }

@@ -66,7 +66,12 @@ inline int mlp_b_off(int l) {
 constexpr int MLP_IMG_W0 = 128 * 16 * 2;
 constexpr int MLP_IMG_WH = 128 * 128 * 2;
 constexpr int MLP_IMG_W4 = 16 * 128 * 2;
-constexpr int MLP_IMG_BYTES = MLP_IMG_W0 + 3 * MLP_IMG_WH + MLP_IMG_W4;  // 106496
+// Bias blocks: N x 16 K-major blocks whose first two K columns hold the
+// bias split into BF16 hi and lo parts (added by one extra MMA K-step).
+constexpr int MLP_IMG_BH = 128 * 16 * 2;
+constexpr int MLP_IMG_B4 = 16 * 16 * 2;
+constexpr int MLP_IMG_BYTES =
+    MLP_IMG_W0 + 3 * MLP_IMG_WH + MLP_IMG_W4 + 3 * MLP_IMG_BH + MLP_IMG_B4;  // 119296
 constexpr int MLP_BIAS_FLOATS = 3 * 128 + 16;
 
 struct MlpNorm { double mu_in[6], inv_sd_in[6], mu_out[6], sd_out[6]; };
@@ -76,8 +81,8 @@ struct MlpNormF { float mu_in[6][2], inv_sd_in[6][2], mu_out[6][2], sd_out[6][2]
 cudaError_t launch_mlp_pack(const float *params, uint8_t *img, float *bias, float *wt,
                             float *wn, cudaStream_t st);
 // err: device word that receives BL_DEVERR_* flags of bounded waits.
-cudaError_t launch_mlp_forward(Soa<float> z, int64_t n, const uint8_t *img, const float *bias,
-                               const MlpNorm &nrm, int num_sms, unsigned *err, cudaStream_t st);
+cudaError_t launch_mlp_forward(Soa<float> z, int64_t n, const uint8_t *img, const MlpNorm &nrm,
+                               int num_sms, unsigned *err, cudaStream_t st);
 cudaError_t mlp_forward_configure();
 
 // Partial-gradient row stride (floats) of the training kernels, padded for

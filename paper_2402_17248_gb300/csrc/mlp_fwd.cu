@@ -3,29 +3,38 @@
 // every particle in place (Sec. 4.3: in-situ inference on device-resident
 // particles, with the normalise / de-normalise data preparation fused).
 //
-// Design (one persistent CTA per SM, two 128-particle tile slots per CTA):
-//  * The five weight matrices (BF16, ~104 KB) are copied once per CTA into
-//    shared memory by bulk async copies and stay there for all tiles. They
-//    are the B operand of every MMA, in the K-major no-swizzle core-matrix
-//    layout prepared by the pack kernel.
+// Design (one persistent CTA per SM, two 128-particle tile slots per CTA,
+// warp-specialised):
+//  * The weight matrices and bias blocks (BF16, ~117 KB) are copied once per
+//    CTA into shared memory by bulk async copies and stay there for all
+//    tiles. They are the B operand of every MMA, in the K-major no-swizzle
+//    core-matrix layout prepared by the pack kernel.
 //  * A tile's activations never leave the SM: each layer's accumulator
-//    D[128 particles x N] is in tensor memory, the epilogue warps read it
-//    (tcgen05.ld), add the bias, apply GELU, round to BF16 and write the
-//    result back into tensor memory (tcgen05.st) as the A operand of the next
-//    layer's MMA (A-from-TMEM form), so shared memory carries only weights.
-//  * Each tile slot (accumulator 128 TMEM columns + activation 64 columns) is
-//    served by two warpgroups that split the 128 features (64 each), and one
-//    elected thread per slot issues its MMAs; the two slots run out of phase,
-//    so one tile's MMAs overlap the other tile's epilogue.
-//  * Epilogue arithmetic: bias add and the GELU argument in packed FP32x2,
-//    tanh on packed BF16 pairs, and 2*GELU = x (1 + tanh) as one BF16x2 FMA.
-//    Hidden activations are stored as 2*GELU(x) and the next layer's weights
-//    are pre-scaled by 1/2 (exact in BF16).
+//    D[128 particles x N] is in tensor memory; epilogue warps read it
+//    (tcgen05.ld), apply GELU, round to BF16 and write the result back into
+//    tensor memory (tcgen05.st) as the A operand of the next layer's MMA
+//    (A-from-TMEM form), so shared memory carries only weights.
+//  * One MMA warp issues every MMA (one elected lane) with descriptors
+//    precomputed once, so a K step costs one 64-bit add; every MMA is
+//    M=128 x N=128 (x K=16), which the tensor core runs at its full rate even
+//    as a dependent accumulation chain (narrower N pays a ~45-cycle minimum
+//    per instruction). Each tile slot is served by two epilogue warpgroups
+//    that own 64 features each; the MMA warp and the warpgroups hand TMEM to
+//    each other through mbarriers (MMA-complete: commit-arrived;
+//    epilogue-complete: 256 thread arrivals). The two slots ping-pong: a
+//    layer's MMAs for one slot run under the other slot's epilogue, which
+//    keeps the special-function unit (tanh) busy.
+//  * Biases ride in the MMA: one extra K=16 step multiplies a constant
+//    shared-memory A matrix whose first two K columns are 1 by the bias split
+//    into BF16 hi and lo parts.
+//  * GELU: u = x (c0 + c1 x^2) in packed FP32x2, tanh.approx.f32, and
+//    2*GELU = x (1 + tanh u) as an FP32x2 FMA, rounded once to BF16. Hidden
+//    activations are stored as 2*GELU(x) and the next layer's weights are
+//    pre-scaled by 1/2 (exact in BF16).
 //  * Inputs are normalised and outputs de-normalised in double-float
 //    arithmetic (FP32 pairs with error-free TwoSum / TwoProd steps), which
 //    carries about 44 bits, i.e. FP64-grade constants and rounding, on the
-//    FP32 pipes; the 7th input column holds 1.0 so the first layer's bias
-//    rides in the K padding.
+//    FP32 pipes.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -37,17 +46,24 @@ namespace bl {
 namespace {
 
 constexpr int SLOTS = 2;
-constexpr int WG_PER_SLOT = 2;
-constexpr int THREADS = 128 * SLOTS * WG_PER_SLOT;
+constexpr int EPI_THREADS = 128 * 2 * SLOTS;       // 4 epilogue warpgroups
+constexpr int THREADS = EPI_THREADS + 32;          // + the MMA warp
+constexpr int MMA_WARP = EPI_THREADS / 32;
 constexpr uint32_t OFF_W0 = 0;
 constexpr uint32_t OFF_W1 = OFF_W0 + MLP_IMG_W0;
 constexpr uint32_t OFF_W4 = OFF_W1 + 3 * MLP_IMG_WH;
-constexpr uint32_t OFF_BIAS = MLP_IMG_BYTES;                      // 106496
-constexpr uint32_t OFF_BAR = OFF_BIAS + MLP_BIAS_FLOATS * 4;      // 108096
-constexpr uint32_t OFF_SLOT = OFF_BAR + 8 * (1 + SLOTS);
+constexpr uint32_t OFF_B1 = OFF_W4 + MLP_IMG_W4;
+constexpr uint32_t OFF_B4 = OFF_B1 + 3 * MLP_IMG_BH;
+constexpr uint32_t OFF_BAR = MLP_IMG_BYTES;  // 1 weights + 2 mma-done + 2 epi-done
+constexpr uint32_t OFF_SLOT = OFF_BAR + 8 * 5;
+constexpr uint32_t OFF_ONES = (OFF_SLOT + 4 + 127) / 128 * 128;  // 128 x 16 BF16 A matrix
+constexpr uint32_t ONES_BYTES = 128 * 16 * 2;
 // Dynamic shared memory requested: more than half of the SM's 228 KB so that
 // exactly one CTA (which owns all 512 TMEM columns) is resident per SM.
-constexpr uint32_t SMEM_BYTES = 120 * 1024;
+constexpr uint32_t SMEM_BYTES = 128 * 1024;
+// TMEM columns of a slot (base 256*slot): accumulator [0,128), activation
+// [128,192).
+constexpr uint32_t COL_ACT = 128;
 
 constexpr float GELU_C0 = 0.7978845608028654f;               // sqrt(2/pi)
 constexpr float GELU_C1 = 0.7978845608028654f * 0.044715f;
@@ -59,28 +75,23 @@ __host__ __device__ inline uint32_t img_off(int n, int k, int K) {
   return (uint32_t)((n >> 3) * (K / 8) * 128 + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2);
 }
 
-// Two hidden features (FP32 accumulators r0, r1 plus bias pair b01) ->
-// packed BF16 pair of 2*GELU: u = x (c0 + c1 x^2) in FP32x2, tanh on packed
-// FP16 pairs (10-bit mantissa), x (1 + tanh u) as one FP32x2 FMA, one
-// rounding to BF16 at the end.
-BL_DEV uint32_t gelu2_pair(uint32_t r0, uint32_t r1, uint64_t b01, bool add_bias) {
+// Two hidden pre-activations (FP32 accumulators r0, r1, bias included) ->
+// packed BF16 pair of 2*GELU: u = x (c0 + c1 x^2) in FP32x2, tanh.approx.f32,
+// x (1 + tanh u) as one FP32x2 FMA, one rounding to BF16 at the end.
+BL_DEV uint32_t gelu2_pair(uint32_t r0, uint32_t r1) {
   uint64_t x, x2, p, u, t, y;
   asm("mov.b64 %0, {%1,%2};" : "=l"(x) : "r"(r0), "r"(r1));
-  if (add_bias) asm("add.rn.f32x2 %0, %1, %2;" : "=l"(x) : "l"(x), "l"(b01));
   asm("mul.rn.f32x2 %0, %1, %1;" : "=l"(x2) : "l"(x));
   const uint64_t c1 = ((uint64_t)__float_as_uint(GELU_C1) << 32) | __float_as_uint(GELU_C1);
   const uint64_t c0 = ((uint64_t)__float_as_uint(GELU_C0) << 32) | __float_as_uint(GELU_C0);
   asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(p) : "l"(x2), "l"(c1), "l"(c0));
   asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(u) : "l"(x), "l"(p));
-  uint32_t ulo, uhi, uh, th, yb;
+  uint32_t ulo, uhi, tlo, thi, ylo, yhi, yb;
   asm("mov.b64 {%0,%1}, %2;" : "=r"(ulo), "=r"(uhi) : "l"(u));
-  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(uh) : "r"(uhi), "r"(ulo));
-  asm("tanh.approx.f16x2 %0, %1;" : "=r"(th) : "r"(uh));
-  asm("{\n .reg .f16 a, b;\n .reg .f32 fa, fb;\n mov.b32 {a, b}, %1;\n"
-      " cvt.f32.f16 fa, a;\n cvt.f32.f16 fb, b;\n mov.b64 %0, {fa, fb};\n}"
-      : "=l"(t) : "r"(th));
+  asm("tanh.approx.f32 %0, %1;" : "=r"(tlo) : "r"(ulo));
+  asm("tanh.approx.f32 %0, %1;" : "=r"(thi) : "r"(uhi));
+  asm("mov.b64 %0, {%1,%2};" : "=l"(t) : "r"(tlo), "r"(thi));
   asm("fma.rn.f32x2 %0, %1, %2, %1;" : "=l"(y) : "l"(x), "l"(t));
-  uint32_t ylo, yhi;
   asm("mov.b64 {%0,%1}, %2;" : "=r"(ylo), "=r"(yhi) : "l"(y));
   asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(yb) : "r"(yhi), "r"(ylo));
   return yb;
@@ -112,29 +123,41 @@ BL_DEV float df_affine(float y, float sh, float sl, float mh, float ml) {
   return s + (se + pe + fmaf(y, sl, ml));
 }
 
+BL_DEV void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 __global__ void __launch_bounds__(THREADS, 1)
 mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__restrict__ img,
-                   const float *__restrict__ bias, MlpNormF nrm, unsigned *err) {
+                   MlpNormF nrm, unsigned *err) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  float *sB = reinterpret_cast<float *>(smem + OFF_BIAS);
   uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + OFF_SLOT);
   const uint32_t sbase = tc::smem_u32(smem);
   const uint32_t bar_w = sbase + OFF_BAR;
+  // mma_done[s] at bar + 8 (1 + s); epi_done[s] at bar + 8 (3 + s)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int wg = warp >> 2, wq = warp & 3;
-  const int slot = wg / WG_PER_SLOT, half = wg % WG_PER_SLOT;
-  const uint32_t bar_m = sbase + OFF_BAR + 8 * (1 + slot);
 
   if (tid == 0) {
     tc::mbar_init(bar_w, 1);
-    for (int s = 0; s < SLOTS; ++s) tc::mbar_init(sbase + OFF_BAR + 8 * (1 + s), 1);
+    for (int s_ = 0; s_ < SLOTS; ++s_) {
+      tc::mbar_init(bar_w + 8 * (1 + s_), 1);
+      tc::mbar_init(bar_w + 8 * (3 + s_), 256);
+    }
     tc::fence_mbar_init();
   }
-  if (warp == 0) {
+  if (warp == MMA_WARP) {
     tc::tmem_alloc(tc::smem_u32(tslot), 512);
     tc::tmem_relinquish();
   }
-  for (int i = tid; i < MLP_BIAS_FLOATS; i += THREADS) sB[i] = bias[i];
+  // constant A operand of the bias step: rows of (1, 1, 0, ..., 0), K-major
+  // core matrices (8 rows x 16 bytes, K chunks 128 bytes apart, row groups
+  // 256 bytes apart)
+  for (int i = tid; i < 128 * 16; i += THREADS) {
+    const int m = i / 16, k = i % 16;
+    *reinterpret_cast<__nv_bfloat16 *>(smem + OFF_ONES + img_off(m, k, 16)) =
+        __float2bfloat16_rn(k < 2 ? 1.0f : 0.0f);
+  }
+  tc::fence_proxy_async();
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
@@ -144,115 +167,141 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
     tc::bulk_g2s(sbase + OFF_W0, img + OFF_W0, MLP_IMG_W0, bar_w);
     for (int l = 0; l < 3; ++l)
       tc::bulk_g2s(sbase + OFF_W1 + l * MLP_IMG_WH, img + OFF_W1 + l * MLP_IMG_WH, MLP_IMG_WH, bar_w);
-    tc::bulk_g2s(sbase + OFF_W4, img + OFF_W4, MLP_IMG_W4, bar_w);
+    tc::bulk_g2s(sbase + OFF_W4, img + OFF_W4, MLP_IMG_W4 + 3 * MLP_IMG_BH + MLP_IMG_B4, bar_w);
   }
-  bool ok = tc::mbar_wait(bar_w, 0, BL_DEVERR_TMA_TIMEOUT, err);
 
-  const uint32_t lane_base = (uint32_t)(wq * 32) << 16;
-  const uint32_t t_acc = tmem + lane_base + slot * 256;
-  const uint32_t t_act = t_acc + 128;
-  const uint32_t d_acc = tmem + slot * 256;  // lane 0 addresses for the MMA
-  const uint32_t d_act = d_acc + 128;
-  const bool issuer = (tid & 255) == 0;
-  constexpr int NSLOT = 128 * WG_PER_SLOT;  // threads per slot
-  constexpr uint32_t ID_H = tc::idesc_bf16(128, 128);
-  constexpr uint32_t ID_O = tc::idesc_bf16(128, 16);
-  uint32_t phase = 0;
-
-  ok = __all_sync(0xffffffffu, ok);
-  for (int64_t tile = (int64_t)blockIdx.x * SLOTS + slot; tile < ntiles;
-       tile += (int64_t)gridDim.x * SLOTS) {
-    const int64_t p = tile * 128 + wq * 32 + lane;
-    const bool valid = p < n;
-    // a failed wait anywhere in the slot stops all of its threads together
-    if (!tc::named_bar_and(1 + slot, NSLOT, ok)) break;
-    // ---- prologue: normalised BF16 input row in TMEM (first warpgroup)
-    if (half == 0) {
-      float xn[6];
+  if (warp == MMA_WARP) {
+    // ------------------------------------------------------------ MMA warp
+    bool ok = __all_sync(0xffffffffu, tc::mbar_wait(bar_w, 0, BL_DEVERR_TMA_TIMEOUT, err));
+    uint32_t ph[SLOTS] = {0, 0};
+    constexpr uint32_t ID_H = tc::idesc_bf16(128, 128);
+    constexpr uint32_t ID_O = tc::idesc_bf16(128, 16);
+    // descriptors of every B operand; a K step adds 256 bytes (16 in the
+    // descriptor's address field, which cannot carry for a 228 KB space)
+    const uint64_t d_ones = tc::sdesc(sbase + OFF_ONES, 128, 256);
+    const uint64_t d_w0 = tc::sdesc(sbase + OFF_W0, 128, 256);
+    uint64_t d_w[4], d_b[4];
+    for (int l = 0; l < 3; ++l) {
+      d_w[l] = tc::sdesc(sbase + OFF_W1 + l * MLP_IMG_WH, 128, 2048);
+      d_b[l] = tc::sdesc(sbase + OFF_B1 + l * MLP_IMG_BH, 128, 256);
+    }
+    d_w[3] = tc::sdesc(sbase + OFF_W4, 128, 2048);
+    d_b[3] = tc::sdesc(sbase + OFF_B4, 128, 256);
+    for (int64_t it = 0;; ++it) {
+      const int64_t t0 = ((int64_t)it * gridDim.x + blockIdx.x) * SLOTS;
+      if (t0 >= ntiles || !ok) break;
+#pragma unroll 1
+      for (int l = 0; l < 5 && ok; ++l) {
+#pragma unroll 1
+        for (int s_ = 0; s_ < SLOTS; ++s_) {
+          if (t0 + s_ >= ntiles) continue;
+          ok = __all_sync(0xffffffffu,
+                          tc::mbar_wait(bar_w + 8 * (3 + s_), ph[s_], BL_DEVERR_MMA_TIMEOUT, err));
+          ph[s_] ^= 1;
+          if (!ok) break;
+          tc::fence_after();
+          const uint32_t acc = tmem + 256 * s_, act = acc + COL_ACT;
+          if (lane == 0) {
+            if (l == 0) {
+              tc::mma_ts(acc, act, d_w0, ID_H, 0);
+            } else {
+              const uint64_t dw = d_w[l - 1];
+              const uint32_t id = (l < 4) ? ID_H : ID_O;
 #pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        const float v = valid ? z.c[c][p] : 0.0f;
-        xn[c] = df_normalise(v, nrm.mu_in[c][0], nrm.mu_in[c][1], nrm.inv_sd_in[c][0],
-                             nrm.inv_sd_in[c][1]);
+              for (int j = 0; j < 8; ++j) tc::mma_ts(acc, act + 8 * j, dw + 16 * j, id, j > 0);
+              tc::mma_ss(acc, d_ones, d_b[l - 1], id, 1);
+            }
+            tc::mma_commit(bar_w + 8 * (1 + s_));
+          }
+          __syncwarp();
+        }
       }
-      uint32_t a[8];
-      a[0] = tc::pack_bf16x2(xn[0], xn[1]);
-      a[1] = tc::pack_bf16x2(xn[2], xn[3]);
-      a[2] = tc::pack_bf16x2(xn[4], xn[5]);
-      a[3] = tc::pack_bf16x2(1.0f, 0.0f);
-      a[4] = a[5] = a[6] = a[7] = 0u;
-      tc::tmem_st8(t_act, a);
+    }
+  } else {
+    // ----------------------------------------------------- epilogue warps
+    const int wg = warp >> 2, wq = warp & 3;
+    const int slot = wg >> 1, h = wg & 1;
+    const uint32_t lane_base = (uint32_t)(wq * 32) << 16;
+    const uint32_t t_acc = tmem + lane_base + 256 * slot;
+    const uint32_t t_act = t_acc + COL_ACT;
+    const uint32_t my_mma = bar_w + 8 * (1 + slot), my_epi = bar_w + 8 * (3 + slot);
+    bool ok = __all_sync(0xffffffffu, tc::mbar_wait(bar_w, 0, BL_DEVERR_TMA_TIMEOUT, err));
+    uint32_t ph = 0;
+    auto done = [&]() {  // hand the TMEM region back to the MMA warp
       tc::tmem_st_wait();
       tc::fence_before();
-    }
-    // ---- five layers
-#pragma unroll 1
-    for (int l = 0; l < 5; ++l) {
-      if (!tc::named_bar_and(1 + slot, NSLOT, ok)) break;
-      if (issuer) {
-        tc::fence_after();
-        if (l == 0) {
-          tc::mma_ts(d_acc, d_act, tc::sdesc(sbase + OFF_W0, 128, 256), ID_H, 0);
-        } else {
-          const uint32_t wb = (l < 4) ? sbase + OFF_W1 + (l - 1) * MLP_IMG_WH : sbase + OFF_W4;
-          const uint32_t id = (l < 4) ? ID_H : ID_O;
-#pragma unroll
-          for (int j = 0; j < 8; ++j)
-            tc::mma_ts(d_acc, d_act + 8 * j, tc::sdesc(wb + 256 * j, 128, 2048), id, j > 0);
-        }
-        tc::mma_commit(bar_m);
-      }
-      __syncwarp();
-      ok = tc::mbar_wait(bar_m, phase, BL_DEVERR_MMA_TIMEOUT, err);
-      ok = __all_sync(0xffffffffu, ok);
-      phase ^= 1;
+      mbar_arrive(my_epi);
+    };
+    auto wait_mma = [&]() {
+      ok = ok && __all_sync(0xffffffffu, tc::mbar_wait(my_mma, ph, BL_DEVERR_MMA_TIMEOUT, err));
+      ph ^= 1;
       tc::fence_after();
-      if (!ok) continue;  // the next barrier stops the slot
-      if (l < 4) {
-        // this warpgroup's 64 features: accumulator columns 64*half ..
-        uint32_t r[2][32];
-        tc::tmem_ld32(t_acc + 64 * half, r[0]);
-        tc::tmem_ld32(t_acc + 64 * half + 32, r[1]);
-        tc::tmem_ld_wait();
-        const bool add_bias = l > 0;
-        const uint64_t *b64 =
-            reinterpret_cast<const uint64_t *>(sB + (l > 0 ? (l - 1) * 128 : 0) + 64 * half);
+    };
+    for (int64_t tile = (int64_t)blockIdx.x * SLOTS + slot; ok && tile < ntiles;
+         tile += (int64_t)gridDim.x * SLOTS) {
+      const int64_t p = tile * 128 + wq * 32 + lane;
+      const bool valid = p < n;
+      if (h == 0) {  // normalised BF16 input row; bias hi/lo columns k = 6, 7
+        float xn[6];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int c = 0; c < 6; ++c) {
+          const float v = valid ? z.c[c][p] : 0.0f;
+          xn[c] = df_normalise(v, nrm.mu_in[c][0], nrm.mu_in[c][1], nrm.inv_sd_in[c][0],
+                               nrm.inv_sd_in[c][1]);
+        }
+        uint32_t a[8];
+        a[0] = tc::pack_bf16x2(xn[0], xn[1]);
+        a[1] = tc::pack_bf16x2(xn[2], xn[3]);
+        a[2] = tc::pack_bf16x2(xn[4], xn[5]);
+        a[3] = tc::pack_bf16x2(1.0f, 1.0f);
+        a[4] = a[5] = a[6] = a[7] = 0u;
+        tc::tmem_st8(t_act, a);
+      }
+      done();  // layer 0 may start
+#pragma unroll 1
+      for (int l = 0; l < 4; ++l) {
+        wait_mma();
+        if (!ok) break;
+        uint32_t r[2][32];
+        tc::tmem_ld32(t_acc + 64 * h, r[0]);
+        tc::tmem_ld32(t_acc + 64 * h + 32, r[1]);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
           uint32_t o[16];
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            o[j] = gelu2_pair(r[h][2 * j], r[h][2 * j + 1], add_bias ? b64[16 * h + j] : 0ull,
-                              add_bias);
-          tc::tmem_st16(t_act + 32 * half + 16 * h, o);
+          for (int j = 0; j < 16; ++j) o[j] = gelu2_pair(r[c][2 * j], r[c][2 * j + 1]);
+          tc::tmem_st16(t_act + 32 * h + 16 * c, o);
         }
-        tc::tmem_st_wait();
-        tc::fence_before();
-      } else if (half == 0) {
+        done();  // layer l+1 may read these features and overwrite the accumulator
+      }
+      if (!ok) break;
+      wait_mma();  // output layer complete
+      if (!ok) break;
+      if (h == 0) {
         uint32_t r[8];
         tc::tmem_ld8(t_acc, r);
         tc::tmem_ld_wait();
         if (valid) {
 #pragma unroll
-          for (int c = 0; c < 6; ++c) {
-            const float yv = __uint_as_float(r[c]) + sB[384 + c];
-            z.c[c][p] = df_affine(yv, nrm.sd_out[c][0], nrm.sd_out[c][1], nrm.mu_out[c][0],
-                                  nrm.mu_out[c][1]);
-          }
+          for (int c = 0; c < 6; ++c)
+            z.c[c][p] = df_affine(__uint_as_float(r[c]), nrm.sd_out[c][0], nrm.sd_out[c][1],
+                                  nrm.mu_out[c][0], nrm.mu_out[c][1]);
         }
-        tc::fence_before();
       }
     }
   }
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
-  if (warp == 0) tc::tmem_dealloc(tmem, 512);
+  if (warp == MMA_WARP) tc::tmem_dealloc(tmem, 512);
 }
 
-// Parameters (flat FP32, layout of mlp_w_off/mlp_b_off) -> BF16 UMMA image,
-// FP32 bias block, and BF16-rounded FP32 copies in [in][out] (wt) and
-// [out][in] (wn) layouts for the SIMT kernels.
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
+  hi = __float2bfloat16_rn(v);
+  lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
 __global__ void mlp_pack_kernel(const float *__restrict__ P, uint8_t *__restrict__ img,
                                 float *__restrict__ bias, float *__restrict__ wt,
                                 float *__restrict__ wn) {
@@ -260,30 +309,58 @@ __global__ void mlp_pack_kernel(const float *__restrict__ P, uint8_t *__restrict
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int stride = gridDim.x * blockDim.x;
   __nv_bfloat16 *im = reinterpret_cast<__nv_bfloat16 *>(img);
-  // layer 0 image: N = 128, K = 16 (6 inputs, bias at column 6, zeros)
+  const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+  // layer 0: N = 128, K = 16 (6 inputs, bias hi/lo at columns 6 and 7, zeros)
   for (int i = tid; i < 128 * 16; i += stride) {
     const int nn = i / 16, k = i % 16;
-    float v = 0.f;
-    if (k < 6) v = P[0 + nn * 6 + k];
-    else if (k == 6) v = P[768 + nn];
-    im[img_off(nn, k, 16) / 2] = __float2bfloat16_rn(v);
+    __nv_bfloat16 v = zero;
+    if (k < 6) v = __float2bfloat16_rn(P[0 + nn * 6 + k]);
+    else if (k < 8) {
+      __nv_bfloat16 hi, lo;
+      split_bf16(P[768 + nn], hi, lo);
+      v = (k == 6) ? hi : lo;
+    }
+    im[img_off(nn, k, 16) / 2] = v;
   }
   // hidden layers 1..3: N = K = 128, weights scaled by 1/2
   const int woff[3] = {896, 17408, 33920};
+  const int boff[3] = {17280, 33792, 50304};
   for (int l = 0; l < 3; ++l) {
-    __nv_bfloat16 *base = im + (MLP_IMG_W0 + l * MLP_IMG_WH) / 2;
+    __nv_bfloat16 *base = im + (OFF_W1 + l * MLP_IMG_WH) / 2;
     for (int i = tid; i < 128 * 128; i += stride) {
       const int nn = i / 128, k = i % 128;
       base[img_off(nn, k, 128) / 2] = __float2bfloat16_rn(0.5f * P[woff[l] + i]);
     }
+    __nv_bfloat16 *bb = im + (OFF_B1 + l * MLP_IMG_BH) / 2;
+    for (int i = tid; i < 128 * 16; i += stride) {
+      const int nn = i / 16, k = i % 16;
+      __nv_bfloat16 v = zero;
+      if (k < 2) {
+        __nv_bfloat16 hi, lo;
+        split_bf16(P[boff[l] + nn], hi, lo);
+        v = (k == 0) ? hi : lo;
+      }
+      bb[img_off(nn, k, 16) / 2] = v;
+    }
   }
-  // layer 4: N = 16 (6 outputs, zero rows), K = 128, scaled by 1/2
+  // layer 4: N = 16 (6 outputs, zero rows), K = 128, scaled by 1/2; bias block
   {
-    __nv_bfloat16 *base = im + (MLP_IMG_W0 + 3 * MLP_IMG_WH) / 2;
+    __nv_bfloat16 *base = im + OFF_W4 / 2;
     for (int i = tid; i < 16 * 128; i += stride) {
       const int nn = i / 128, k = i % 128;
       const float v = nn < 6 ? 0.5f * P[50432 + nn * 128 + k] : 0.f;
       base[img_off(nn, k, 128) / 2] = __float2bfloat16_rn(v);
+    }
+    __nv_bfloat16 *bb = im + OFF_B4 / 2;
+    for (int i = tid; i < 16 * 16; i += stride) {
+      const int nn = i / 16, k = i % 16;
+      __nv_bfloat16 v = zero;
+      if (nn < 6 && k < 2) {
+        __nv_bfloat16 hi, lo;
+        split_bf16(P[51200 + nn], hi, lo);
+        v = (k == 0) ? hi : lo;
+      }
+      bb[img_off(nn, k, 16) / 2] = v;
     }
   }
   for (int i = tid; i < MLP_BIAS_FLOATS; i += stride) {
@@ -403,8 +480,8 @@ static void split_df(double v, float *hl) {
   hl[1] = (float)(v - (double)hl[0]);
 }
 
-cudaError_t launch_mlp_forward(Soa<float> z, int64_t n, const uint8_t *img, const float *bias,
-                               const MlpNorm &nrm64, int num_sms, unsigned *err, cudaStream_t st) {
+cudaError_t launch_mlp_forward(Soa<float> z, int64_t n, const uint8_t *img, const MlpNorm &nrm64,
+                               int num_sms, unsigned *err, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   MlpNormF nrm;
   for (int c = 0; c < 6; ++c) {
@@ -416,7 +493,7 @@ cudaError_t launch_mlp_forward(Soa<float> z, int64_t n, const uint8_t *img, cons
   const int64_t ntiles = (n + 127) / 128;
   int64_t grid = (ntiles + SLOTS - 1) / SLOTS;
   if (grid > num_sms) grid = num_sms;
-  mlp_forward_kernel<<<(unsigned)grid, THREADS, SMEM_BYTES, st>>>(z, n, ntiles, img, bias, nrm, err);
+  mlp_forward_kernel<<<(unsigned)grid, THREADS, SMEM_BYTES, st>>>(z, n, ntiles, img, nrm, err);
   return cudaGetLastError();
 }
 
@@ -440,3 +517,4 @@ extern "C" int bl_debug_umma_probe(const void *A, const void *B, float *D, int N
       (const __nv_bfloat16 *)A, (const __nv_bfloat16 *)B, D, N, K, ks, ns, lbo, sbo);
   return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }
+
