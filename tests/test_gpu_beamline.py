@@ -1,0 +1,198 @@
+"""GPU parity of the surrogate beamline paths: the adjoint bl_track_grad
+against the FP64 oracle's reverse mode and finite differences, batched uneven
+bunches with per-bunch quadrupoles through surrogate stages, and what a
+network trained on the GPU gains over the plain pusher it replaces."""
+import math
+import time
+
+import numpy as np
+import pytest
+
+from gpu_util import KEYS, as_f32, from_bunch, to_bunch
+from oracle import adjoint, beamline, mlp, moments
+from synth import lattice
+from synth.bunch import BunchRecipe, gaussian_bunch, mlp_init, training_population
+
+pytestmark = pytest.mark.gpu
+WIDTHS = [6, 128, 128, 128, 128, 6]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    from paper_2402_17248_gb300 import bl
+    bl.lib()
+
+
+def _bunch(n, seed=0):
+    z, g = gaussian_bunch(BunchRecipe(n=n, seed=seed))
+    return as_f32([z[k] for k in KEYS]), g
+
+
+def _near_identity(seed, eps=0.05):
+    """Weights of F(z) = z + eps * (a random smooth map), exactly representable
+    in BF16 on the identity path: hidden units 0..5 carry GELU(x) and 6..11
+    carry GELU(-x), and GELU(x) - GELU(-x) = x for the tanh form as well."""
+    Ws, bs = mlp_init(WIDTHS, seed)
+    Ws = [eps * W for W in Ws]
+    bs = [eps * b for b in bs]
+    I6 = np.eye(6)
+    Ws[0][:12, :] = np.vstack([I6, -I6])
+    bs[0][:12] = 0.0
+    for l in (1, 2, 3):
+        Ws[l][:12, :] = 0.0
+        Ws[l][:12, :12] = np.block([[I6, -I6], [-I6, I6]])
+        bs[l][:12] = 0.0
+    Ws[4][:, :12] = np.hstack([I6, -I6])
+    return Ws, bs
+
+
+def _nets(z, n_stages, seed):
+    """Well-conditioned test surrogates (GPU handles and matching oracle objects)."""
+    from paper_2402_17248_gb300 import bl
+    Z = np.stack(z, axis=1)
+    mu, sd = Z.mean(axis=0), Z.std(axis=0)
+    gpu, ora = [], []
+    for s in range(n_stages):
+        Ws, bs = _near_identity(seed + s)
+        gpu.append(bl.Surrogate(Ws, bs, mu, sd, mu, sd))
+        Wr = [mlp.bf16_round(np.asarray(W, np.float32).astype(np.float64)) for W in Ws]
+        br = [np.asarray(b, np.float32).astype(np.float64) for b in bs]
+        ora.append(mlp.Surrogate(Wr, br, mu, sd, mu, sd))
+    return gpu, ora
+
+
+def _beamline(n_stages, nets, k=lattice.DESIGN_K):
+    els = []
+    for s in range(n_stages):
+        st = lattice.plasma(400)
+        st["surrogate"] = nets[s]
+        els.append(st)
+        els.extend(lattice.matching_section(k))
+    return els
+
+
+@pytest.mark.parametrize("which", ["eps_n_x", "sigma_x", "eps_n_y"])
+def test_adjoint_matches_oracle(which):
+    from paper_2402_17248_gb300 import bl
+    z, g = _bunch(10000, seed=3)
+    gpu, ora = _nets(z, 2, 40)
+    L = bl.Lattice(_beamline(2, gpu))
+    b = to_bunch(z, g)
+    J, grad = bl.bl_track_grad(b, L, which)
+    Jo, go = adjoint.track_grad(z, g, _beamline(2, ora), which, bf16=True)
+    rel = np.max(np.abs(grad[0] - go)) / np.max(np.abs(go))
+    print("%s: J gpu %.6e oracle %.6e; dJ/dk normwise rel err %.3e" % (which, J[0], Jo, rel))
+    assert abs(J[0] / Jo - 1) < 1e-5
+    # the device VJP differentiates GELU through tanh.approx (relative error
+    # ~2^-11 per evaluation) over 8 layers; the oracle uses exact tanh
+    assert rel < 5e-3
+
+
+def test_adjoint_matches_finite_differences():
+    from paper_2402_17248_gb300 import bl
+    z, g = _bunch(10000, seed=4)
+    gpu, ora = _nets(z, 1, 60)
+    els_o = _beamline(1, ora)
+    L = bl.Lattice(_beamline(1, gpu))
+    J, grad = bl.bl_track_grad(to_bunch(z, g), L, "sigma_x")
+    fd = []
+    for qi in range(4):
+        idx = [i for i, e in enumerate(els_o) if e["kind"] == "quad"][qi]
+        k = els_o[idx]["k"]
+        h = 1e-6 * abs(k)
+        vals = []
+        for sgn in (1, -1):
+            e2 = [dict(e) for e in els_o]
+            e2[idx]["k"] = k + sgn * h
+            vals.append(adjoint.track_objective(z, g, e2, "sigma_x", bf16=True))
+        fd.append((vals[0] - vals[1]) / (2 * h))
+    fd = np.array(fd)
+    rel = np.max(np.abs(grad[0] - fd)) / np.max(np.abs(fd))
+    print("dJ/dk vs central differences of the oracle: normwise rel err %.3e" % rel)
+    assert rel < 2e-3
+
+
+def test_batched_uneven_bunches_per_bunch_quads():
+    from paper_2402_17248_gb300 import bl
+    counts = [20000, 3, 0, 4097, 15000, 1]
+    off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    z, g = _bunch(int(off[-1]), seed=5)
+    gpu, ora = _nets(z, 2, 80)
+    rng = np.random.default_rng(0)
+    kq = rng.uniform(20, 80, size=(len(counts), 8)) * np.array([-1, 1, -1, 1] * 2)
+    def els_for(nets, per_bunch=None, b=None):
+        out = _beamline(2, nets)
+        qi = 0
+        for e in out:
+            if e["kind"] == "quad":
+                if per_bunch is not None:
+                    e["per_bunch_k"] = kq[:, qi].copy()
+                else:
+                    e["k"] = float(kq[b, qi])
+                qi += 1
+        return out
+    L = bl.Lattice(els_for(gpu, per_bunch=True), n_bunch_k=len(counts))
+    bb = to_bunch(z, g, offsets=off)
+    mom, nonfin = bl.bl_track(bb, L)
+    got = from_bunch(bb)
+    for b in range(len(counts)):
+        sl = slice(off[b], off[b + 1])
+        zb = [c[sl] for c in z]
+        zo, go, snaps = beamline.track(zb, g, els_for(ora, b=b), bf16=True)
+        for a, w in zip(got, zo):
+            if counts[b]:
+                # FP32 segment maps differ from the FP64 oracle by ~1e-7; a
+                # stage input that close to a BF16 rounding midpoint rounds
+                # the other way (one BF16 ulp, 2^-8 relative) for a handful
+                # of particles, so bound the outlier fraction and their size
+                sc = max(np.std(w), np.max(np.abs(w)))
+                err = np.abs(a[sl] - w) / sc
+                assert np.mean(err > 1e-5) <= 2e-3
+                assert np.max(err) <= 2e-2
+        for e, (want, gr) in enumerate(snaps):
+            m = mom[e][b]
+            assert m[0] == counts[b]
+            if counts[b] > 1:
+                S = moments.sigma_matrix(want)
+                sd = np.sqrt(np.diag(S))
+                for j, (p, q) in enumerate(moments.PAIRS):
+                    assert abs(m[7 + j] - want[7 + j]) <= 1e-4 * sd[p] * sd[q]
+
+
+def test_trained_surrogate_gain_over_pusher():
+    """A surrogate of a 15 GeV plasma stage, trained on the GPU from pusher
+    pairs, replaces the 400-step RK4 push at a fraction of its cost, with the
+    held-out exit beam's moments close to the pusher's."""
+    import torch
+    from paper_2402_17248_gb300 import bl, workflow
+    kp = 59507.379801365234
+    g0 = 1.0 + 15000.0 / 0.51099895
+    zt, _ = training_population(16, 65536, g0, 0.2 / kp, seed=1001)
+    pairs = workflow.stage_pairs(workflow.device_bunch(zt, g0), lattice.staged_beamline(1, 400))
+    xin, xout, gin = pairs[0]
+    sur, info = workflow.fit_surrogate(xin, xout, steps=6000, batch=4096, lr=2e-3, seed=5)
+    print("15 GeV stage surrogate test loss %.3e" % info["test_loss"])
+    ntrain = info["train_pairs"]
+    test_in = xin[:, ntrain:].contiguous()
+    st = lattice.plasma(400)
+    def run(push):
+        b = bl.Bunch([test_in[i].clone() for i in range(6)], gin)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        if push:
+            bl.bl_push_stage(b, st)
+        else:
+            bl.bl_surrogate_apply(sur, b)
+        torch.cuda.synchronize()
+        return b, time.perf_counter() - t
+    run(True), run(False)
+    bp, tp = run(True)
+    bs, ts = run(False)
+    g_out = bl.bl_reference_exit(st, gin)
+    qp = bl.bl_beam_quantities(bl.bl_moments(bp)[0], g_out)
+    qs = bl.bl_beam_quantities(bl.bl_moments(bs)[0], g_out)
+    err = {k: abs(qs[k] / qp[k] - 1) for k in ("eps_n_x", "eps_n_y", "rel_energy_spread", "sigma_x")}
+    print("speedup %.1fx; relative moment differences %s" % (tp / ts, err))
+    assert tp / ts > 5
+    assert info["test_loss"] < 0.05
+    assert err["rel_energy_spread"] < 0.05
