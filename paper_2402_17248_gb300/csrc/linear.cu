@@ -84,6 +84,129 @@ stream_kernel(Soa<T> zin, Soa<T> zout, int64_t n, const int64_t *__restrict__ of
   }
 }
 
+// FP32 particles with moments: two warps share each group of 32 particles. The
+// even warp of a pair accumulates sums 0..13 (6 linear sums, 8 products) and
+// writes output rows 0..2; the odd warp accumulates sums 14..26 and writes
+// rows 3..5. Splitting the 27 float-float accumulators this way halves the
+// registers per thread, so more warps keep loads in flight. Roles are
+// warp-uniform, so no lane diverges. Because the update is in place and each
+// warp reads all six coordinates, the pair meets at a 64-thread named barrier
+// between its loads and its stores.
+template <int J0, int J1>
+BL_DEV void mom_subset(float (&hi)[J1 - J0], float (&lo)[J1 - J0], const float (&v)[6]) {
+#pragma unroll
+  for (int a = 0; a < 6; ++a)
+    if (a >= J0 && a < J1) ff_add(hi[a - J0], lo[a - J0], v[a]);
+  int j = 6;
+#pragma unroll
+  for (int a = 0; a < 6; ++a)
+#pragma unroll
+    for (int b = a; b < 6; ++b) {
+      if (j >= J0 && j < J1) ff_add_prod(hi[j - J0], lo[j - J0], v[a], v[b]);
+      ++j;
+    }
+}
+
+// One role's share of a (bunch, block) piece: accumulate, then reduce the
+// role's sums across its warp; lane 0 leaves them in red[warp][0..13].
+template <bool APPLY, int ROLE>
+BL_DEV void mom_piece(Soa<float> &zin, Soa<float> &zout, int64_t lo_p, int64_t hi_p, int plane,
+                      const float *__restrict__ Mb, const float *__restrict__ cb,
+                      double (*red)[15]) {
+  constexpr int J0 = ROLE ? 14 : 0, J1 = ROLE ? 27 : 14;
+  float M[18], c[6], shi[J1 - J0], slo[J1 - J0];
+  if (APPLY) {
+#pragma unroll
+    for (int i = 0; i < 18; ++i) M[i] = __ldg(Mb + 18 * ROLE + i);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) c[i] = cb ? __ldg(cb + i) : 0.0f;
+  }
+#pragma unroll
+  for (int i = 0; i < J1 - J0; ++i) { shi[i] = 0.f; slo[i] = 0.f; }
+  float nf = 0.f;
+  const int pair = threadIdx.x >> 6;
+  const int64_t last = (hi_p - lo_p - 1) / (STREAM_THREADS / 2) * (STREAM_THREADS / 2);
+  // every warp of the pair runs the same trip count (the tail is masked, not
+  // skipped) so the pair barrier is always matched
+#pragma unroll 2
+  for (int64_t q = 0; q <= last; q += STREAM_THREADS / 2) {
+    const int64_t p = lo_p + q + plane;
+    const bool in = p < hi_p;
+    float v[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) v[i] = in ? zin.c[i][p] : 0.0f;
+    if (in) {
+      mom_subset<J0, J1>(shi, slo, v);
+      if (ROLE == 0) nf += finite6(v) ? 0.f : 1.f;
+    }
+    if (APPLY) asm volatile("bar.sync %0, 64;" ::"r"(1 + pair) : "memory");
+    if (APPLY && in) {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) v[i] -= c[i];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        float acc = 0.f;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) acc = fmaf(M[i * 6 + j], v[j], acc);
+        zout.c[3 * ROLE + i][p] = acc;
+      }
+    }
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < J1 - J0; ++i) {
+    const double t = warp_sum((double)shi[i] + (double)slo[i]);
+    if (lane == 0) red[warp][i] = t;
+  }
+  if (ROLE == 0) {
+    const double t = warp_sum((double)nf);
+    if (lane == 0) red[warp][14] = t;
+  }
+}
+
+template <bool APPLY>
+__global__ void __launch_bounds__(STREAM_THREADS, 3)
+stream_mom_f32_kernel(Soa<float> zin, Soa<float> zout, int64_t n,
+                      const int64_t *__restrict__ offsets, int n_bunch,
+                      const float *__restrict__ mats, int per_bunch,
+                      const float *__restrict__ centers, double *__restrict__ partials) {
+  __shared__ int s_b0;
+  __shared__ double s_red[STREAM_THREADS / 32][15];
+  const int64_t start = (int64_t)blockIdx.x * STREAM_CHUNK;
+  const int64_t end = min(n, start + STREAM_CHUNK);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int role = warp & 1;
+  const int plane = (warp >> 1) * 32 + lane;  // particle lane 0..127
+  if (threadIdx.x == 0) s_b0 = find_bunch(offsets, n_bunch, start);
+  __syncthreads();
+  int b = s_b0;
+  int64_t lo = start;
+  while (lo < end) {
+    const int64_t hi = min(end, bunch_end(offsets, b, n));
+    if (hi > lo) {
+      const float *Mb = APPLY ? mats + (per_bunch ? (int64_t)b * 36 : 0) : nullptr;
+      const float *cb = (APPLY && centers) ? centers + (int64_t)b * 6 : nullptr;
+      if (role == 0) mom_piece<APPLY, 0>(zin, zout, lo, hi, plane, Mb, cb, s_red);
+      else mom_piece<APPLY, 1>(zin, zout, lo, hi, plane, Mb, cb, s_red);
+      __syncthreads();
+      if (threadIdx.x < 28) {
+        // sum j: role-0 warps hold j < 14 (and the non-finite count at 14),
+        // role-1 warps hold j >= 14 at j - 14
+        const int j = threadIdx.x;
+        const int r = (j >= 14 && j < 27) ? 1 : 0;
+        const int k = (j == 27) ? 14 : (r ? j - 14 : j);
+        double t = 0.0;
+        for (int w = r; w < STREAM_THREADS / 32; w += 2) t += s_red[w][k];
+        partials[((int64_t)b + blockIdx.x) * 28 + j] = t;
+      }
+      __syncthreads();
+    }
+    lo = max(lo, hi);
+    ++b;
+    if (b >= n_bunch) break;
+  }
+}
+
 template <typename T>
 cudaError_t launch_stream(Soa<T> zin, Soa<T> zout, int64_t n, const int64_t *offsets,
                           int n_bunch, const T *mats, int per_bunch, const T *centers,
@@ -91,6 +214,15 @@ cudaError_t launch_stream(Soa<T> zin, Soa<T> zout, int64_t n, const int64_t *off
   if (n <= 0) return cudaSuccess;
   const int64_t nb = stream_blocks(n);
   dim3 grid((unsigned)nb), block(STREAM_THREADS);
+  if constexpr (sizeof(T) == 4) {
+    if (moments) {
+      if (apply)
+        stream_mom_f32_kernel<true><<<grid, block, 0, st>>>(zin, zout, n, offsets, n_bunch, mats, per_bunch, centers, partials);
+      else
+        stream_mom_f32_kernel<false><<<grid, block, 0, st>>>(zin, zout, n, offsets, n_bunch, mats, per_bunch, centers, partials);
+      return cudaGetLastError();
+    }
+  }
   if (apply && moments)
     stream_kernel<T, true, true><<<grid, block, 0, st>>>(zin, zout, n, offsets, n_bunch, mats, per_bunch, centers, partials);
   else if (apply)
