@@ -213,8 +213,9 @@ def main():
     del pairs
     torch.cuda.empty_cache()
 
-    # ---- the tracked bunch
-    z, g = gaussian_bunch(BunchRecipe(n=n, seed=0))
+    # ---- the tracked bunch: rank r tracks particles [r n, (r+1) n) of one
+    # world*n-particle bunch (weak scaling, no exchange in the data path)
+    z, g = gaussian_bunch(BunchRecipe(n=n, seed=0, first_index=rank * n))
     z0 = [torch.tensor(z[k], dtype=torch.float32, device=dev) for k in KEYS]
     host_pinned = [torch.tensor(z[k], dtype=torch.float32).pin_memory() for k in KEYS]
     del z
@@ -242,6 +243,10 @@ def main():
     m_push, nf_push = bl.bl_track(bunch, lat_push)
     torch.cuda.synchronize()
     g_final = bunch.gamma_ref
+    if world > 1:  # moments of the whole bunch from the per-rank moments
+        from paper_2402_17248_gb300.shard import gather_moments
+        m_sur = gather_moments(m_sur)
+        m_push = gather_moments(m_push)
     d_sur = bl.bl_beam_quantities(m_sur[-1][0], g_final)
     d_push = bl.bl_beam_quantities(m_push[-1][0], g_final)
     moment_err = {k: abs(d_sur[k] / d_push[k] - 1) for k in d_push}

@@ -33,6 +33,7 @@ class BunchRecipe:
     rel_energy_spread: float = 0.01
     t_cut_sigma: float = 3.0        # |t| truncation in units of sigma_t
     seed: int = 0
+    first_index: int = 0            # Philox index of the first particle (for shards)
 
     @property
     def gamma_ref(self):
@@ -82,7 +83,8 @@ def gaussian_bunch(recipe: BunchRecipe):
     spx = recipe.eps_n / (recipe.sigma_x * bg)
     st = C_LIGHT * recipe.sigma_t_s
     spt = recipe.rel_energy_spread * g / bg
-    z = _draw(recipe.n, recipe.seed, 0, recipe.sigma_x, spx, st, spt, recipe.t_cut_sigma)
+    z = _draw(recipe.n, recipe.seed, recipe.first_index, recipe.sigma_x, spx, st, spt,
+              recipe.t_cut_sigma)
     return z, g
 
 
