@@ -36,6 +36,10 @@ N_STAGES = 8
 STEPS_PER_STAGE = 400
 FLOP_PER_PARTICLE_STAGE = 2 * (6 * 128 + 3 * 128 * 128 + 128 * 6)  # 101,376
 SEG_BYTES_PER_PARTICLE = 48
+# DRAM bytes (read + write) per particle of mlp_forward_kernel from one ncu
+# capture of the current kernel on 8,388,608 particles (201.6 MB + 140.0 MB),
+# scaled per particle; see profiles/mlp_forward_kernel_8M_particles.md
+MLP_DRAM_BYTES_PER_PARTICLE = (201.610240e6 + 140.004352e6) / 8388608
 KEYS = ("x", "px", "y", "py", "t", "pt")
 
 
@@ -379,7 +383,8 @@ def main():
         "speedup_vs_pusher": value / push_value,
         "moment_rel_err_vs_pusher": moment_err,
         "roofline": {"bound": "tensor", "achieved": mlp_tflops, "peak": bf16_peak,
-                     "unit": "TFLOP/s", "frac": mlp_tflops / bf16_peak, "traffic": None,
+                     "unit": "TFLOP/s", "frac": mlp_tflops / bf16_peak,
+                     "traffic": MLP_DRAM_BYTES_PER_PARTICLE * n,
                      "kernel": "mlp_forward_kernel", "peak_source": peak_src + " bf16 burst",
                      "ms_per_launch": mlp_ms},
         "roofline_segment": {"bound": "hbm", "achieved": seg_gbs, "peak": hbm_peak, "unit": "GB/s",
