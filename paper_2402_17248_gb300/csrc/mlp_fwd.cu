@@ -3,27 +3,27 @@
 // every particle in place (Sec. 4.3: in-situ inference on device-resident
 // particles, with the normalise / de-normalise data preparation fused).
 //
-// Design (one persistent CTA per SM, two 128-particle tile slots per CTA,
+// Design (one persistent CTA per SM, three 128-particle tile slots per CTA,
 // warp-specialised):
 //  * The weight matrices and bias blocks (BF16, ~117 KB) are copied once per
 //    CTA into shared memory by bulk async copies and stay there for all
 //    tiles. They are the B operand of every MMA, in the K-major no-swizzle
 //    core-matrix layout prepared by the pack kernel.
-//  * A tile's activations never leave the SM: each layer's accumulator
-//    D[128 particles x N] is in tensor memory; epilogue warps read it
-//    (tcgen05.ld), apply GELU, round to BF16 and write the result back into
-//    tensor memory (tcgen05.st) as the A operand of the next layer's MMA
-//    (A-from-TMEM form), so shared memory carries only weights.
+//  * A tile's activations never leave the SM. Each layer's accumulator
+//    D[128 particles x N] (FP32) is in tensor memory, 128 columns per slot;
+//    the slot's epilogue warpgroup reads it (tcgen05.ld), applies GELU,
+//    rounds to BF16 and writes the row into the slot's 32 KB activation
+//    buffer in shared memory, in the same K-major core-matrix layout as the
+//    weights: the A operand of the next layer's MMA. Keeping activations out
+//    of tensor memory leaves room for three tiles in flight, so the MMAs of
+//    one tile and the tanh work of the two others overlap.
 //  * One MMA warp issues every MMA (one elected lane) with descriptors
-//    precomputed once, so a K step costs one 64-bit add; every MMA is
-//    M=128 x N=128 (x K=16), which the tensor core runs at its full rate even
-//    as a dependent accumulation chain (narrower N pays a ~45-cycle minimum
-//    per instruction). Each tile slot is served by two epilogue warpgroups
-//    that own 64 features each; the MMA warp and the warpgroups hand TMEM to
-//    each other through mbarriers (MMA-complete: commit-arrived;
-//    epilogue-complete: 256 thread arrivals). The two slots ping-pong: a
-//    layer's MMAs for one slot run under the other slot's epilogue, which
-//    keeps the special-function unit (tanh) busy.
+//    precomputed once, so a K step costs one 64-bit add; every hidden-layer
+//    MMA is M=128 x N=128 (x K=16), which the tensor core runs at its full
+//    rate even as a dependent accumulation chain with both operands in
+//    shared memory. The MMA warp and the warpgroups hand buffers to each
+//    other through mbarriers (MMA-complete: commit-arrived; epilogue-complete:
+//    128 thread arrivals).
 //  * Biases ride in the MMA: one extra K=16 step multiplies a constant
 //    shared-memory A matrix whose first two K columns are 1 by the bias split
 //    into BF16 hi and lo parts.
@@ -34,7 +34,8 @@
 //  * Inputs are normalised and outputs de-normalised in double-float
 //    arithmetic (FP32 pairs with error-free TwoSum / TwoProd steps), which
 //    carries about 44 bits, i.e. FP64-grade constants and rounding, on the
-//    FP32 pipes.
+//    FP32 pipes. A slot's next inputs are loaded from HBM while the current
+//    tile is in the network.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -45,8 +46,8 @@ namespace bl {
 
 namespace {
 
-constexpr int SLOTS = 2;
-constexpr int EPI_THREADS = 128 * 2 * SLOTS;       // 4 epilogue warpgroups
+constexpr int SLOTS = 3;
+constexpr int EPI_THREADS = 128 * SLOTS;           // one epilogue warpgroup per slot
 constexpr int THREADS = EPI_THREADS + 32;          // + the MMA warp
 constexpr int MMA_WARP = EPI_THREADS / 32;
 constexpr uint32_t OFF_W0 = 0;
@@ -54,16 +55,18 @@ constexpr uint32_t OFF_W1 = OFF_W0 + MLP_IMG_W0;
 constexpr uint32_t OFF_W4 = OFF_W1 + 3 * MLP_IMG_WH;
 constexpr uint32_t OFF_B1 = OFF_W4 + MLP_IMG_W4;
 constexpr uint32_t OFF_B4 = OFF_B1 + 3 * MLP_IMG_BH;
-constexpr uint32_t OFF_BAR = MLP_IMG_BYTES;  // 1 weights + 2 mma-done + 2 epi-done
-constexpr uint32_t OFF_SLOT = OFF_BAR + 8 * 5;
-constexpr uint32_t OFF_ONES = (OFF_SLOT + 4 + 127) / 128 * 128;  // 128 x 16 BF16 A matrix
+constexpr uint32_t ACT_BYTES = 128 * 128 * 2;      // one slot's BF16 activations
+constexpr uint32_t OFF_ACT = (MLP_IMG_BYTES + 1023) / 1024 * 1024;
+constexpr uint32_t OFF_ONES = OFF_ACT + SLOTS * ACT_BYTES;  // 128 x 16 BF16 A matrix
 constexpr uint32_t ONES_BYTES = 128 * 16 * 2;
-// Dynamic shared memory requested: more than half of the SM's 228 KB so that
-// exactly one CTA (which owns all 512 TMEM columns) is resident per SM.
-constexpr uint32_t SMEM_BYTES = 128 * 1024;
-// TMEM columns of a slot (base 256*slot): accumulator [0,128), activation
-// [128,192).
-constexpr uint32_t COL_ACT = 128;
+constexpr uint32_t OFF_BAR = OFF_ONES + ONES_BYTES;  // 1 weights + 3 mma-done + 3 epi-done
+constexpr uint32_t OFF_SLOT = OFF_BAR + 8 * (1 + 2 * SLOTS);
+constexpr uint32_t SMEM_BYTES = (OFF_SLOT + 4 + 127) / 128 * 128;
+static_assert(SMEM_BYTES <= 227 * 1024, "shared memory budget");
+static_assert(SMEM_BYTES > 114 * 1024, "one CTA per SM (it owns all tensor memory)");
+// Tensor memory: 128 FP32 accumulator columns per slot.
+constexpr uint32_t TMEM_COLS = 512;
+static_assert(128 * SLOTS <= TMEM_COLS, "tensor memory budget");
 
 constexpr float GELU_C0 = 0.7978845608028654f;               // sqrt(2/pi)
 constexpr float GELU_C1 = 0.7978845608028654f * 0.044715f;
@@ -95,6 +98,20 @@ BL_DEV uint32_t gelu2_pair(uint32_t r0, uint32_t r1) {
   asm("mov.b64 {%0,%1}, %2;" : "=r"(ylo), "=r"(yhi) : "l"(y));
   asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(yb) : "r"(yhi), "r"(ylo));
   return yb;
+}
+
+// GELU of 32 consecutive accumulator columns (features 32c .. 32c+31 of one
+// particle row), written as four 16-byte K chunks of the row in the
+// activation buffer (row base `row`, chunks 128 bytes apart).
+BL_DEV void gelu_chunk(const uint32_t (&r)[32], uint32_t row, int c) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const uint32_t a = gelu2_pair(r[8 * q + 0], r[8 * q + 1]);
+    const uint32_t b = gelu2_pair(r[8 * q + 2], r[8 * q + 3]);
+    const uint32_t d = gelu2_pair(r[8 * q + 4], r[8 * q + 5]);
+    const uint32_t e = gelu2_pair(r[8 * q + 6], r[8 * q + 7]);
+    tc::st_shared_v4(row + (uint32_t)(4 * c + q) * 128, a, b, d, e);
+  }
 }
 
 // Double-float helpers: a value v is carried as hi + lo (FP32 each).
@@ -134,19 +151,19 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
   uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + OFF_SLOT);
   const uint32_t sbase = tc::smem_u32(smem);
   const uint32_t bar_w = sbase + OFF_BAR;
-  // mma_done[s] at bar + 8 (1 + s); epi_done[s] at bar + 8 (3 + s)
+  // mma_done[s] at bar + 8 (1 + s); epi_done[s] at bar + 8 (1 + SLOTS + s)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (tid == 0) {
     tc::mbar_init(bar_w, 1);
     for (int s_ = 0; s_ < SLOTS; ++s_) {
       tc::mbar_init(bar_w + 8 * (1 + s_), 1);
-      tc::mbar_init(bar_w + 8 * (3 + s_), 256);
+      tc::mbar_init(bar_w + 8 * (1 + SLOTS + s_), 128);
     }
     tc::fence_mbar_init();
   }
   if (warp == MMA_WARP) {
-    tc::tmem_alloc(tc::smem_u32(tslot), 512);
+    tc::tmem_alloc(tc::smem_u32(tslot), TMEM_COLS);
     tc::tmem_relinquish();
   }
   // constant A operand of the bias step: rows of (1, 1, 0, ..., 0), K-major
@@ -173,20 +190,18 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
   if (warp == MMA_WARP) {
     // ------------------------------------------------------------ MMA warp
     bool ok = __all_sync(0xffffffffu, tc::mbar_wait(bar_w, 0, BL_DEVERR_TMA_TIMEOUT, err));
-    uint32_t ph[SLOTS] = {0, 0};
+    uint32_t ph = 0;  // bit s: expected phase of epi_done[s]
     constexpr uint32_t ID_H = tc::idesc_bf16(128, 128);
     constexpr uint32_t ID_O = tc::idesc_bf16(128, 16);
-    // descriptors of every B operand; a K step adds 256 bytes (16 in the
+    // descriptors of every operand; a K step adds 256 bytes (16 in the
     // descriptor's address field, which cannot carry for a 228 KB space)
     const uint64_t d_ones = tc::sdesc(sbase + OFF_ONES, 128, 256);
     const uint64_t d_w0 = tc::sdesc(sbase + OFF_W0, 128, 256);
-    uint64_t d_w[4], d_b[4];
-    for (int l = 0; l < 3; ++l) {
-      d_w[l] = tc::sdesc(sbase + OFF_W1 + l * MLP_IMG_WH, 128, 2048);
-      d_b[l] = tc::sdesc(sbase + OFF_B1 + l * MLP_IMG_BH, 128, 256);
-    }
-    d_w[3] = tc::sdesc(sbase + OFF_W4, 128, 2048);
-    d_b[3] = tc::sdesc(sbase + OFF_B4, 128, 256);
+    // layers 1..4: W1, W2, W3, W4 are MLP_IMG_WH bytes apart, and so are the
+    // bias blocks B1..B4 at MLP_IMG_BH (the descriptor address is in 16 B units)
+    static_assert(OFF_W4 == OFF_W1 + 3 * MLP_IMG_WH && OFF_B4 == OFF_B1 + 3 * MLP_IMG_BH, "image");
+    const uint64_t d_w1 = tc::sdesc(sbase + OFF_W1, 128, 2048);
+    const uint64_t d_b1 = tc::sdesc(sbase + OFF_B1, 128, 256);
     for (int64_t it = 0;; ++it) {
       const int64_t t0 = ((int64_t)it * gridDim.x + blockIdx.x) * SLOTS;
       if (t0 >= ntiles || !ok) break;
@@ -195,21 +210,24 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
 #pragma unroll 1
         for (int s_ = 0; s_ < SLOTS; ++s_) {
           if (t0 + s_ >= ntiles) continue;
-          ok = __all_sync(0xffffffffu,
-                          tc::mbar_wait(bar_w + 8 * (3 + s_), ph[s_], BL_DEVERR_MMA_TIMEOUT, err));
-          ph[s_] ^= 1;
+          ok = __all_sync(0xffffffffu, tc::mbar_wait(bar_w + 8 * (1 + SLOTS + s_), (ph >> s_) & 1u,
+                                                     BL_DEVERR_MMA_TIMEOUT, err));
+          ph ^= 1u << s_;
           if (!ok) break;
           tc::fence_after();
-          const uint32_t acc = tmem + 256 * s_, act = acc + COL_ACT;
+          const uint32_t acc = tmem + 128 * s_;
+          const uint32_t act = sbase + OFF_ACT + s_ * ACT_BYTES;
           if (lane == 0) {
             if (l == 0) {
-              tc::mma_ts(acc, act, d_w0, ID_H, 0);
+              tc::mma_ss(acc, tc::sdesc(act, 128, 256), d_w0, ID_H, 0);
             } else {
-              const uint64_t dw = d_w[l - 1];
+              const uint64_t da = tc::sdesc(act, 128, 2048);
+              const uint64_t dw = d_w1 + (uint64_t)((l - 1) * (MLP_IMG_WH >> 4));
+              const uint64_t db = d_b1 + (uint64_t)((l - 1) * (MLP_IMG_BH >> 4));
               const uint32_t id = (l < 4) ? ID_H : ID_O;
 #pragma unroll
-              for (int j = 0; j < 8; ++j) tc::mma_ts(acc, act + 8 * j, dw + 16 * j, id, j > 0);
-              tc::mma_ss(acc, d_ones, d_b[l - 1], id, 1);
+              for (int j = 0; j < 8; ++j) tc::mma_ss(acc, da + 16 * j, dw + 16 * j, id, j > 0);
+              tc::mma_ss(acc, d_ones, db, id, 1);
             }
             tc::mma_commit(bar_w + 8 * (1 + s_));
           }
@@ -218,17 +236,18 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
       }
     }
   } else {
-    // ----------------------------------------------------- epilogue warps
-    const int wg = warp >> 2, wq = warp & 3;
-    const int slot = wg >> 1, h = wg & 1;
-    const uint32_t lane_base = (uint32_t)(wq * 32) << 16;
-    const uint32_t t_acc = tmem + lane_base + 256 * slot;
-    const uint32_t t_act = t_acc + COL_ACT;
-    const uint32_t my_mma = bar_w + 8 * (1 + slot), my_epi = bar_w + 8 * (3 + slot);
+    // ------------------------------------------------------ epilogue warps
+    const int slot = warp >> 2, wq = warp & 3;
+    const int m = wq * 32 + lane;  // this thread's particle row within a tile
+    const uint32_t t_acc = tmem + ((uint32_t)(wq * 32) << 16) + 128 * slot;
+    const uint32_t act = sbase + OFF_ACT + slot * ACT_BYTES;
+    const uint32_t row_in = act + (uint32_t)((m >> 3) * 256 + (m & 7) * 16);    // K = 16 layout
+    const uint32_t row_h = act + (uint32_t)((m >> 3) * 2048 + (m & 7) * 16);    // K = 128 layout
+    const uint32_t my_mma = bar_w + 8 * (1 + slot), my_epi = bar_w + 8 * (1 + SLOTS + slot);
     bool ok = __all_sync(0xffffffffu, tc::mbar_wait(bar_w, 0, BL_DEVERR_TMA_TIMEOUT, err));
     uint32_t ph = 0;
-    auto done = [&]() {  // hand the TMEM region back to the MMA warp
-      tc::tmem_st_wait();
+    auto done = [&]() {  // hand the activation buffer and the accumulator to the MMA warp
+      tc::fence_proxy_async();
       tc::fence_before();
       mbar_arrive(my_epi);
     };
@@ -237,64 +256,70 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
       ph ^= 1;
       tc::fence_after();
     };
-    for (int64_t tile = (int64_t)blockIdx.x * SLOTS + slot; ok && tile < ntiles;
-         tile += (int64_t)gridDim.x * SLOTS) {
-      const int64_t p = tile * 128 + wq * 32 + lane;
+    const int64_t tstride = (int64_t)gridDim.x * SLOTS;
+    int64_t tile = (int64_t)blockIdx.x * SLOTS + slot;
+    float xin[6];
+    {
+      const int64_t p = tile * 128 + m;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) xin[c] = (tile < ntiles && p < n) ? z.c[c][p] : 0.0f;
+    }
+    for (; ok && tile < ntiles; tile += tstride) {
+      const int64_t p = tile * 128 + m;
       const bool valid = p < n;
-      if (h == 0) {  // normalised BF16 input row; bias hi/lo columns k = 6, 7
+      {  // normalised BF16 input row; bias hi/lo columns k = 6, 7; k = 8..15 zero
         float xn[6];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) {
-          const float v = valid ? z.c[c][p] : 0.0f;
-          xn[c] = df_normalise(v, nrm.mu_in[c][0], nrm.mu_in[c][1], nrm.inv_sd_in[c][0],
+        for (int c = 0; c < 6; ++c)
+          xn[c] = df_normalise(xin[c], nrm.mu_in[c][0], nrm.mu_in[c][1], nrm.inv_sd_in[c][0],
                                nrm.inv_sd_in[c][1]);
-        }
-        uint32_t a[8];
-        a[0] = tc::pack_bf16x2(xn[0], xn[1]);
-        a[1] = tc::pack_bf16x2(xn[2], xn[3]);
-        a[2] = tc::pack_bf16x2(xn[4], xn[5]);
-        a[3] = tc::pack_bf16x2(1.0f, 1.0f);
-        a[4] = a[5] = a[6] = a[7] = 0u;
-        tc::tmem_st8(t_act, a);
+        tc::st_shared_v4(row_in, tc::pack_bf16x2(xn[0], xn[1]), tc::pack_bf16x2(xn[2], xn[3]),
+                         tc::pack_bf16x2(xn[4], xn[5]), tc::pack_bf16x2(1.0f, 1.0f));
+        tc::st_shared_v4(row_in + 128, 0u, 0u, 0u, 0u);
       }
       done();  // layer 0 may start
+      {  // prefetch this slot's next tile while the current one is in the network
+        const int64_t tn = tile + tstride, pn = tn * 128 + m;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) xin[c] = (tn < ntiles && pn < n) ? z.c[c][pn] : 0.0f;
+      }
 #pragma unroll 1
       for (int l = 0; l < 4; ++l) {
         wait_mma();
         if (!ok) break;
-        uint32_t r[2][32];
-        tc::tmem_ld32(t_acc + 64 * h, r[0]);
-        tc::tmem_ld32(t_acc + 64 * h + 32, r[1]);
-        tc::tmem_ld_wait();
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          uint32_t o[16];
-#pragma unroll
-          for (int j = 0; j < 16; ++j) o[j] = gelu2_pair(r[c][2 * j], r[c][2 * j + 1]);
-          tc::tmem_st16(t_act + 32 * h + 16 * c, o);
-        }
-        done();  // layer l+1 may read these features and overwrite the accumulator
+        uint32_t ra[32], rb[32];
+        tc::tmem_ld32(t_acc, ra);
+        tc::tmem_ld_wait_regs(ra);
+        tc::tmem_ld32(t_acc + 32, rb);
+        gelu_chunk(ra, row_h, 0);
+        tc::tmem_ld_wait_regs(rb);
+        tc::tmem_ld32(t_acc + 64, ra);
+        gelu_chunk(rb, row_h, 1);
+        tc::tmem_ld_wait_regs(ra);
+        tc::tmem_ld32(t_acc + 96, rb);
+        gelu_chunk(ra, row_h, 2);
+        tc::tmem_ld_wait_regs(rb);
+        gelu_chunk(rb, row_h, 3);
+        done();  // layer l+1 may read these activations and overwrite the accumulator
       }
       if (!ok) break;
       wait_mma();  // output layer complete
       if (!ok) break;
-      if (h == 0) {
-        uint32_t r[8];
-        tc::tmem_ld8(t_acc, r);
-        tc::tmem_ld_wait();
-        if (valid) {
+      uint32_t r[8];
+      tc::tmem_ld8(t_acc, r);
+      tc::tmem_ld_wait();
+      if (valid) {
 #pragma unroll
-          for (int c = 0; c < 6; ++c)
-            z.c[c][p] = df_affine(__uint_as_float(r[c]), nrm.sd_out[c][0], nrm.sd_out[c][1],
-                                  nrm.mu_out[c][0], nrm.mu_out[c][1]);
-        }
+        for (int c = 0; c < 6; ++c)
+          z.c[c][p] = df_affine(__uint_as_float(r[c]), nrm.sd_out[c][0], nrm.sd_out[c][1],
+                                nrm.mu_out[c][0], nrm.mu_out[c][1]);
       }
     }
   }
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
-  if (warp == MMA_WARP) tc::tmem_dealloc(tmem, 512);
+  if (warp == MMA_WARP) tc::tmem_dealloc(tmem, TMEM_COLS);
 }
 
 __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
