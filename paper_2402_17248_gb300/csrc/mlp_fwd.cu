@@ -17,8 +17,8 @@
 //    weights: the A operand of the next layer's MMA. Keeping activations out
 //    of tensor memory leaves room for three tiles in flight, so the MMAs of
 //    one tile and the tanh work of the two others overlap.
-//  * One MMA warp issues every MMA (one elected lane) with descriptors
-//    precomputed once, so a K step costs one 64-bit add; every hidden-layer
+//  * One lane of the MMA warp issues every MMA with descriptors precomputed
+//    once, so a K step costs one 64-bit add; every hidden-layer
 //    MMA is M=128 x N=128 (x K=16), which the tensor core runs at its full
 //    rate even as a dependent accumulation chain with both operands in
 //    shared memory. The MMA warp and the warpgroups hand buffers to each
@@ -47,7 +47,10 @@ namespace bl {
 namespace {
 
 constexpr int SLOTS = 3;
-constexpr int EPI_THREADS = 128 * SLOTS;           // one epilogue warpgroup per slot
+constexpr int WG_PER_SLOT = 2;                     // epilogue warpgroups per slot
+constexpr int FEAT_WG = 128 / WG_PER_SLOT;         // hidden features per warpgroup
+constexpr int CHUNK = 16;                          // accumulator columns per tcgen05.ld
+constexpr int EPI_THREADS = 128 * WG_PER_SLOT * SLOTS;
 constexpr int THREADS = EPI_THREADS + 32;          // + the MMA warp
 constexpr int MMA_WARP = EPI_THREADS / 32;
 constexpr uint32_t OFF_W0 = 0;
@@ -100,17 +103,18 @@ BL_DEV uint32_t gelu2_pair(uint32_t r0, uint32_t r1) {
   return yb;
 }
 
-// GELU of 32 consecutive accumulator columns (features 32c .. 32c+31 of one
-// particle row), written as four 16-byte K chunks of the row in the
-// activation buffer (row base `row`, chunks 128 bytes apart).
-BL_DEV void gelu_chunk(const uint32_t (&r)[32], uint32_t row, int c) {
+// GELU of CH consecutive accumulator columns (features f0 .. f0+CH-1 of one
+// particle row), written as CH/8 16-byte K chunks of the row in the
+// activation buffer (row base `row`, K chunks 128 bytes apart).
+template <int CH>
+BL_DEV void gelu_chunk(const uint32_t (&r)[CH], uint32_t row, int f0) {
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < CH / 8; ++q) {
     const uint32_t a = gelu2_pair(r[8 * q + 0], r[8 * q + 1]);
     const uint32_t b = gelu2_pair(r[8 * q + 2], r[8 * q + 3]);
     const uint32_t d = gelu2_pair(r[8 * q + 4], r[8 * q + 5]);
     const uint32_t e = gelu2_pair(r[8 * q + 6], r[8 * q + 7]);
-    tc::st_shared_v4(row + (uint32_t)(4 * c + q) * 128, a, b, d, e);
+    tc::st_shared_v4(row + (uint32_t)(f0 / 8 + q) * 128, a, b, d, e);
   }
 }
 
@@ -144,7 +148,13 @@ BL_DEV void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-__global__ void __launch_bounds__(THREADS, 1)
+// Registers: the 4 sub-partitions of the SM each hold a quarter of the 64K
+// registers, and warp w runs on sub-partition w % 4, so the MMA warp makes
+// sub-partition 0 host one warp more than the others.
+constexpr int WARPS_SMSP0 = (THREADS / 32 + 3) / 4;
+constexpr int MAX_REGS = (16384 / (32 * WARPS_SMSP0)) / 8 * 8;
+
+__global__ void __maxnreg__(MAX_REGS)
 mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__restrict__ img,
                    MlpNormF nrm, unsigned *err) {
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -158,7 +168,7 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
     tc::mbar_init(bar_w, 1);
     for (int s_ = 0; s_ < SLOTS; ++s_) {
       tc::mbar_init(bar_w + 8 * (1 + s_), 1);
-      tc::mbar_init(bar_w + 8 * (1 + SLOTS + s_), 128);
+      tc::mbar_init(bar_w + 8 * (1 + SLOTS + s_), 128 * WG_PER_SLOT);
     }
     tc::fence_mbar_init();
   }
@@ -189,55 +199,66 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
 
   if (warp == MMA_WARP) {
     // ------------------------------------------------------------ MMA warp
-    bool ok = __all_sync(0xffffffffu, tc::mbar_wait(bar_w, 0, BL_DEVERR_TMA_TIMEOUT, err));
-    uint32_t ph = 0;  // bit s: expected phase of epi_done[s]
-    constexpr uint32_t ID_H = tc::idesc_bf16(128, 128);
-    constexpr uint32_t ID_O = tc::idesc_bf16(128, 16);
-    // descriptors of every operand; a K step adds 256 bytes (16 in the
-    // descriptor's address field, which cannot carry for a 228 KB space)
-    const uint64_t d_ones = tc::sdesc(sbase + OFF_ONES, 128, 256);
-    const uint64_t d_w0 = tc::sdesc(sbase + OFF_W0, 128, 256);
-    // layers 1..4: W1, W2, W3, W4 are MLP_IMG_WH bytes apart, and so are the
-    // bias blocks B1..B4 at MLP_IMG_BH (the descriptor address is in 16 B units)
-    static_assert(OFF_W4 == OFF_W1 + 3 * MLP_IMG_WH && OFF_B4 == OFF_B1 + 3 * MLP_IMG_BH, "image");
-    const uint64_t d_w1 = tc::sdesc(sbase + OFF_W1, 128, 2048);
-    const uint64_t d_b1 = tc::sdesc(sbase + OFF_B1, 128, 256);
-    for (int64_t it = 0;; ++it) {
-      const int64_t t0 = ((int64_t)it * gridDim.x + blockIdx.x) * SLOTS;
-      if (t0 >= ntiles || !ok) break;
-#pragma unroll 1
-      for (int l = 0; l < 5 && ok; ++l) {
-#pragma unroll 1
-        for (int s_ = 0; s_ < SLOTS; ++s_) {
-          if (t0 + s_ >= ntiles) continue;
-          ok = __all_sync(0xffffffffu, tc::mbar_wait(bar_w + 8 * (1 + SLOTS + s_), (ph >> s_) & 1u,
-                                                     BL_DEVERR_MMA_TIMEOUT, err));
-          ph ^= 1u << s_;
-          if (!ok) break;
-          tc::fence_after();
-          const uint32_t acc = tmem + 128 * s_;
-          const uint32_t act = sbase + OFF_ACT + s_ * ACT_BYTES;
-          if (lane == 0) {
-            if (l == 0) {
-              tc::mma_ss(acc, tc::sdesc(act, 128, 256), d_w0, ID_H, 0);
-            } else {
-              const uint64_t da = tc::sdesc(act, 128, 2048);
-              const uint64_t dw = d_w1 + (uint64_t)((l - 1) * (MLP_IMG_WH >> 4));
-              const uint64_t db = d_b1 + (uint64_t)((l - 1) * (MLP_IMG_BH >> 4));
-              const uint32_t id = (l < 4) ? ID_H : ID_O;
+    // One lane runs the whole issue loop: the 5 layers x SLOTS batches of a
+    // tile round are unrolled, so every descriptor is a register plus a
+    // compile-time offset and nothing but the epilogue-complete wait stands
+    // between two batches.
+    if (lane == 0) {
+      bool ok = tc::mbar_wait(bar_w, 0, BL_DEVERR_TMA_TIMEOUT, err);
+      uint32_t ph = 0;  // bit s: expected phase of epi_done[s]
+      constexpr uint32_t ID_H = tc::idesc_bf16(128, 128);
+      constexpr uint32_t ID_O = tc::idesc_bf16(128, 16);
+      // descriptors of every operand; a K step adds 256 bytes (16 in the
+      // descriptor's address field, which cannot carry for a 228 KB space)
+      const uint64_t d_ones = tc::sdesc(sbase + OFF_ONES, 128, 256);
+      const uint64_t d_w0 = tc::sdesc(sbase + OFF_W0, 128, 256);
+      // layers 1..4: W1, W2, W3, W4 are MLP_IMG_WH bytes apart, and so are the
+      // bias blocks B1..B4 at MLP_IMG_BH (the descriptor address is in 16 B units)
+      static_assert(OFF_W4 == OFF_W1 + 3 * MLP_IMG_WH && OFF_B4 == OFF_B1 + 3 * MLP_IMG_BH, "image");
+      const uint64_t d_w1 = tc::sdesc(sbase + OFF_W1, 128, 2048);
+      const uint64_t d_b1 = tc::sdesc(sbase + OFF_B1, 128, 256);
+      // activation buffers: K = 16 layout for the input (layer 0), K = 128 after
+      const uint64_t d_in0 = tc::sdesc(sbase + OFF_ACT, 128, 256);
+      const uint64_t d_act0 = tc::sdesc(sbase + OFF_ACT, 128, 2048);
+      constexpr uint64_t ACT_STEP = ACT_BYTES >> 4;
+      for (int64_t t0 = (int64_t)blockIdx.x * SLOTS; ok && t0 < ntiles;
+           t0 += (int64_t)gridDim.x * SLOTS) {
+        const int64_t live = ntiles - t0;  // slots s < live hold a tile this round
 #pragma unroll
-              for (int j = 0; j < 8; ++j) tc::mma_ss(acc, da + 16 * j, dw + 16 * j, id, j > 0);
-              tc::mma_ss(acc, d_ones, db, id, 1);
+        for (int l = 0; l < 5; ++l) {
+#pragma unroll
+          for (int s_ = 0; s_ < SLOTS; ++s_) {
+            if (s_ < live && ok) {
+              ok = tc::mbar_wait(bar_w + 8 * (1 + SLOTS + s_), (ph >> s_) & 1u,
+                                 BL_DEVERR_MMA_TIMEOUT, err);
+              ph ^= 1u << s_;
+              if (ok) {
+                tc::fence_after();
+                const uint32_t acc = tmem + 128 * s_;
+                if (l == 0) {
+                  tc::mma_ss(acc, d_in0 + s_ * ACT_STEP, d_w0, ID_H, 0);
+                } else {
+                  const uint64_t da = d_act0 + s_ * ACT_STEP;
+                  const uint64_t dw = d_w1 + (uint64_t)((l - 1) * (MLP_IMG_WH >> 4));
+                  const uint64_t db = d_b1 + (uint64_t)((l - 1) * (MLP_IMG_BH >> 4));
+                  const uint32_t id = (l < 4) ? ID_H : ID_O;
+#pragma unroll
+                  for (int j = 0; j < 8; ++j) tc::mma_ss(acc, da + 16 * j, dw + 16 * j, id, j > 0);
+                  tc::mma_ss(acc, d_ones, db, id, 1);
+                }
+                tc::mma_commit(bar_w + 8 * (1 + s_));
+              }
             }
-            tc::mma_commit(bar_w + 8 * (1 + s_));
           }
-          __syncwarp();
         }
       }
     }
+    __syncwarp();
   } else {
     // ------------------------------------------------------ epilogue warps
-    const int slot = warp >> 2, wq = warp & 3;
+    const int wg = warp >> 2, wq = warp & 3;
+    const int slot = wg / WG_PER_SLOT, h = wg % WG_PER_SLOT;
+    const bool io = (h == 0);  // this warpgroup loads inputs and stores outputs
     const int m = wq * 32 + lane;  // this thread's particle row within a tile
     const uint32_t t_acc = tmem + ((uint32_t)(wq * 32) << 16) + 128 * slot;
     const uint32_t act = sbase + OFF_ACT + slot * ACT_BYTES;
@@ -262,12 +283,12 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
     {
       const int64_t p = tile * 128 + m;
 #pragma unroll
-      for (int c = 0; c < 6; ++c) xin[c] = (tile < ntiles && p < n) ? z.c[c][p] : 0.0f;
+      for (int c = 0; c < 6; ++c) xin[c] = (io && tile < ntiles && p < n) ? z.c[c][p] : 0.0f;
     }
     for (; ok && tile < ntiles; tile += tstride) {
       const int64_t p = tile * 128 + m;
       const bool valid = p < n;
-      {  // normalised BF16 input row; bias hi/lo columns k = 6, 7; k = 8..15 zero
+      if (io) {  // normalised BF16 input row; bias hi/lo columns k = 6, 7; k = 8..15 zero
         float xn[6];
 #pragma unroll
         for (int c = 0; c < 6; ++c)
@@ -278,7 +299,7 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
         tc::st_shared_v4(row_in + 128, 0u, 0u, 0u, 0u);
       }
       done();  // layer 0 may start
-      {  // prefetch this slot's next tile while the current one is in the network
+      if (io) {  // prefetch this slot's next tile while the current one is in the network
         const int64_t tn = tile + tstride, pn = tn * 128 + m;
 #pragma unroll
         for (int c = 0; c < 6; ++c) xin[c] = (tn < ntiles && pn < n) ? z.c[c][pn] : 0.0f;
@@ -287,24 +308,28 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
       for (int l = 0; l < 4; ++l) {
         wait_mma();
         if (!ok) break;
-        uint32_t ra[32], rb[32];
-        tc::tmem_ld32(t_acc, ra);
+        // this warpgroup's FEAT_WG features in chunks of CHUNK columns; the
+        // next chunk's load is in flight while the current one is computed
+        const int f_base = h * FEAT_WG;
+        uint32_t ra[CHUNK], rb[CHUNK];
+        tc::tmem_ld(t_acc + f_base, ra);
         tc::tmem_ld_wait_regs(ra);
-        tc::tmem_ld32(t_acc + 32, rb);
-        gelu_chunk(ra, row_h, 0);
-        tc::tmem_ld_wait_regs(rb);
-        tc::tmem_ld32(t_acc + 64, ra);
-        gelu_chunk(rb, row_h, 1);
-        tc::tmem_ld_wait_regs(ra);
-        tc::tmem_ld32(t_acc + 96, rb);
-        gelu_chunk(ra, row_h, 2);
-        tc::tmem_ld_wait_regs(rb);
-        gelu_chunk(rb, row_h, 3);
+#pragma unroll
+        for (int c = 0; c < FEAT_WG / CHUNK; c += 2) {
+          const int f = f_base + c * CHUNK;
+          tc::tmem_ld(t_acc + f + CHUNK, rb);
+          gelu_chunk<CHUNK>(ra, row_h, f);
+          tc::tmem_ld_wait_regs(rb);
+          if (c + 2 < FEAT_WG / CHUNK) tc::tmem_ld(t_acc + f + 2 * CHUNK, ra);
+          gelu_chunk<CHUNK>(rb, row_h, f + CHUNK);
+          if (c + 2 < FEAT_WG / CHUNK) tc::tmem_ld_wait_regs(ra);
+        }
         done();  // layer l+1 may read these activations and overwrite the accumulator
       }
       if (!ok) break;
       wait_mma();  // output layer complete
       if (!ok) break;
+      if (!io) continue;
       uint32_t r[8];
       tc::tmem_ld8(t_acc, r);
       tc::tmem_ld_wait();
