@@ -37,9 +37,9 @@ STEPS_PER_STAGE = 400
 FLOP_PER_PARTICLE_STAGE = 2 * (6 * 128 + 3 * 128 * 128 + 128 * 6)  # 101,376
 SEG_BYTES_PER_PARTICLE = 48
 # DRAM bytes (read + write) per particle of mlp_forward_kernel from one ncu
-# capture of the current kernel on 8,388,608 particles (201.6 MB + 140.0 MB),
+# capture of the current kernel on 8,388,608 particles (201.6 MB + 139.6 MB),
 # scaled per particle; see profiles/mlp_forward_kernel_8M_particles.md
-MLP_DRAM_BYTES_PER_PARTICLE = (201.610240e6 + 140.004352e6) / 8388608
+MLP_DRAM_BYTES_PER_PARTICLE = (201.623296e6 + 139.620352e6) / 8388608
 KEYS = ("x", "px", "y", "py", "t", "pt")
 
 
@@ -59,8 +59,10 @@ def parse():
     p.add_argument("--train-lr", type=float, default=2e-3)
     p.add_argument("--train-pairs", type=int, default=1 << 22)
     p.add_argument("--pusher-steps", type=int, default=2)
-    p.add_argument("--cpu-sample", type=int, default=1 << 13)
+    p.add_argument("--cpu-sample", type=int, default=1 << 16)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the batched-bunch, adjoint and training side measurements")
     return p.parse_args()
 
 
@@ -168,6 +170,110 @@ def run_reference(args):
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ------------------------------------------------------------ side measurements
+def side_measurements(args, bl, workflow, lattice, surs, infos, z0, g, elements, dev):
+    """Throughput of the other paths on the hot-path list, reported beside the
+    headline (not part of it): surrogate training, the batched uneven-bunch
+    beamline with per-bunch quadrupoles and the adjoint."""
+    import torch
+    from synth.bunch import random_quad_magnitudes, uneven_counts
+    out = {}
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    # training: samples per second of bl_surrogate_train_step (wall clock of
+    # the whole fit, held-out loss evaluations included)
+    steps = sum(i["steps"] for i in infos)
+    secs = sum(i["seconds"] for i in infos)
+    out["training"] = {"samples_per_s": steps * args.train_batch / secs, "batch": args.train_batch,
+                       "steps": steps, "seconds": secs,
+                       "kernels": "mlp_grad_kernel + reduce_adam_kernel + mlp_pack_kernel per step"}
+
+    # batched: 256 bunches with log-uniform counts in [1e4, 1e6] and 32 quad
+    # strengths each (magnitudes U[20, 80], signs -,+,-,+), stored back to
+    # back, through the 8-stage surrogate beamline with per-bunch moments after
+    # every element. Bunch b's particles are counts[b] consecutive particles
+    # of the 2^24 pool starting at a seeded offset (wrapping), so no new host
+    # draw is needed.
+    nbunch = 256
+    counts = uneven_counts(nbunch, 1.0e4, 1.0e6, seed=0)
+    off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    ntot = int(off[-1])
+    pool = z0[0].numel()
+    rng = np.random.default_rng(0)
+    starts = rng.integers(0, pool, size=nbunch)
+    idx = np.concatenate([(st + np.arange(c)) % pool for st, c in zip(starts, counts)])
+    idx_d = torch.tensor(idx, device=dev)
+    zb0 = [c.index_select(0, idx_d) for c in z0]
+    del idx_d
+    zb = [c.clone() for c in zb0]
+    bb = bl.Bunch(zb, g, offsets=off)
+    kmag = random_quad_magnitudes(nbunch, 32, 20.0, 80.0, seed=0)
+    signs = np.array([-1.0, 1.0, -1.0, 1.0] * 8)
+    els = workflow.surrogate_beamline(elements, surs)
+    qi = 0
+    for e in els:
+        if e["kind"] == "quad":
+            e["per_bunch_k"] = (signs[qi] * kmag[:, qi]).copy()
+            qi += 1
+    lat_b = bl.Lattice(els, n_bunch_k=nbunch)
+
+    def step_b():
+        for w, s0 in zip(zb, zb0):
+            w.copy_(s0, non_blocking=True)
+        bb.struct.gamma_ref = g
+        return bl.bl_track(bb, lat_b, moments=True)
+
+    step_b()
+    torch.cuda.synchronize()
+    kb = 3
+    ev[0].record(stream)
+    for _ in range(kb):
+        m_b, nf_b = step_b()
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    b_ms = ev[0].elapsed_time(ev[1]) / kb
+    out["batched"] = {"value": ntot * N_STAGES / (b_ms * 1e-3), "unit": "particle-stages/s",
+                      "ms_per_step": b_ms, "particles": ntot, "bunches": nbunch,
+                      "snapshots_per_bunch": len(m_b), "nonfinite": int(nf_b),
+                      "workload": "256 bunches, counts floor(exp(U[ln 1e4, ln 1e6])), per-bunch "
+                                  "quad strengths, 8 surrogate stages, per-bunch moments after "
+                                  "every element"}
+    del zb, zb0, bb
+    torch.cuda.empty_cache()
+
+    # adjoint: d eps_n,x / dk for the 32 quads of the 8-stage surrogate
+    # beamline on the first 2^22 particles (forward with checkpoints, reverse
+    # sweep, FP64 reductions)
+    na = min(1 << 22, z0[0].numel())
+    za0 = [c[:na].clone() for c in z0]
+    za = [c.clone() for c in za0]
+    ba = bl.Bunch(za, g)
+    lat_a = bl.Lattice(workflow.surrogate_beamline(elements, surs))
+
+    def step_a():
+        for w, s0 in zip(za, za0):
+            w.copy_(s0, non_blocking=True)
+        ba.struct.gamma_ref = g
+        return bl.bl_track_grad(ba, lat_a, "eps_n_x")
+
+    step_a()
+    torch.cuda.synchronize()
+    ka = 3
+    t = time.perf_counter()
+    for _ in range(ka):
+        J, grad = step_a()
+    torch.cuda.synchronize()
+    a_ms = 1e3 * (time.perf_counter() - t) / ka
+    out["adjoint"] = {"value": na * N_STAGES / (a_ms * 1e-3), "unit": "particle-stages/s",
+                      "ms_per_gradient": a_ms, "particles": na, "quads": int(grad.shape[1]),
+                      "objective": "eps_n_x", "J": float(J[0]),
+                      "timing": "host wall clock per bl_track_grad call (it returns host values)"}
+    del za, za0, ba
+    torch.cuda.empty_cache()
+    return out
 
 
 # ------------------------------------------------------------------- GPU arm
@@ -343,6 +449,10 @@ def main():
     h2d = 6 * 4 * n
     d2h = 6 * 4 * n + nel * 28 * 8
 
+    extras = {}
+    if world == 1 and not args.no_extras:
+        extras = side_measurements(args, bl, workflow, lattice, surs, infos, z0, g, elements, dev)
+
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -394,6 +504,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": "particle-stages/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "gpu_launches": launches_per_step * args.steps,
+        **extras,
         "clocks": clk,
         "nonfinite": nf,
     }
