@@ -138,7 +138,11 @@ bl_status bl_track_grad(bl_bunch *b, const bl_lattice *lat_c, int32_t objective,
     const auto &gr = L->groups[gi];
     if (gr.stage) {
       const bl_surrogate *s = L->els[gr.first].surrogate;
-      BL_CUDA(launch_mlp_vjp(ckpt(gi), lm, n, s->wt, s->wn, s->nrm, st));
+      if (!ctx->mlp_vjp_configured) {
+        BL_CUDA(mlp_vjp_configure());
+        ctx->mlp_vjp_configured = true;
+      }
+      BL_CUDA(launch_mlp_vjp(ckpt(gi), lm, n, s->img, s->nrm, ctx->num_sms, ctx->err_word, st));
     } else {
       const float *mats = (const float *)((const uint8_t *)P.d_mats + P.mat_off[gi]);
       BL_CUDA(launch_linear_adjoint<float>(lm, ckpt(gi), n, off, nbunch, mats, per_bunch,

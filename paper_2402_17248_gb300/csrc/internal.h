@@ -108,9 +108,11 @@ cudaError_t launch_mlp_loss(const float *in, const float *out, int64_t ld, const
                             double *loss_partials, int *nblocks_out, cudaStream_t st);
 cudaError_t launch_loss_finalize(const double *loss_partials, int nblocks, int64_t count,
                                  double *loss_out, cudaStream_t st);
-// lam <- J_F(zin)^T lam for every particle (raw coordinates on both sides).
-cudaError_t launch_mlp_vjp(Soa<float> zin, Soa<float> lam, int64_t n, const float *wt,
-                           const float *wn, const MlpNorm &nrm, cudaStream_t st);
+// lam <- J_F(zin)^T lam for every particle (raw coordinates on both sides),
+// on the tensor cores with the inference weight image (mlp_vjp.cu).
+cudaError_t launch_mlp_vjp(Soa<float> zin, Soa<float> lam, int64_t n, const uint8_t *img,
+                           const MlpNorm &nrm, int num_sms, unsigned *err, cudaStream_t st);
+cudaError_t mlp_vjp_configure();
 
 
 }  // namespace bl

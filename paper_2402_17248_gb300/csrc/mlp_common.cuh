@@ -1,0 +1,102 @@
+// Device helpers and the shared-memory weight-image layout common to the
+// surrogate inference kernel (mlp_fwd.cu) and its vector-Jacobian product
+// (mlp_vjp.cu).
+#pragma once
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "internal.h"
+#include "tc.cuh"
+
+namespace bl {
+namespace mlp {
+
+// Byte offsets of the BF16 weight image (built by mlp_pack_kernel): W0, W1..W3,
+// W4, then the bias blocks B1..B3, B4.
+constexpr uint32_t OFF_W0 = 0;
+constexpr uint32_t OFF_W1 = OFF_W0 + MLP_IMG_W0;
+constexpr uint32_t OFF_W4 = OFF_W1 + 3 * MLP_IMG_WH;
+constexpr uint32_t OFF_B1 = OFF_W4 + MLP_IMG_W4;
+constexpr uint32_t OFF_B4 = OFF_B1 + 3 * MLP_IMG_BH;
+static_assert(OFF_W4 == OFF_W1 + 3 * MLP_IMG_WH && OFF_B4 == OFF_B1 + 3 * MLP_IMG_BH, "image");
+
+constexpr float GELU_C0 = 0.7978845608028654f;               // sqrt(2/pi)
+constexpr float GELU_C1 = 0.7978845608028654f * 0.044715f;
+
+// Byte offset of element (n, k) of an [N x K] K-major BF16 block in the
+// no-swizzle core-matrix layout: 8x8 core matrices of 128 contiguous bytes,
+// adjacent along K at 128 bytes, adjacent along N at (K/8)*128 bytes.
+__host__ __device__ inline uint32_t img_off(int n, int k, int K) {
+  return (uint32_t)((n >> 3) * (K / 8) * 128 + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2);
+}
+
+// Double-float helpers: a value v is carried as hi + lo (FP32 each).
+BL_DEV void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+}
+
+// (z - mu) * inv with mu = mh + ml and inv = ih + il, rounded to FP32.
+BL_DEV float df_normalise(float z, float mh, float ml, float ih, float il) {
+  float dh, dl;
+  two_sum(z, -mh, dh, dl);
+  dl -= ml;
+  const float p = dh * ih;
+  const float pe = fmaf(dh, ih, -p);
+  return p + (pe + fmaf(dh, il, dl * ih));
+}
+
+// y * sd + mu with sd = sh + sl and mu = mh + ml, rounded to FP32.
+BL_DEV float df_affine(float y, float sh, float sl, float mh, float ml) {
+  const float p = y * sh;
+  const float pe = fmaf(y, sh, -p);
+  float s, se;
+  two_sum(p, mh, s, se);
+  return s + (se + pe + fmaf(y, sl, ml));
+}
+
+BL_DEV void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+
+// Constant A operand of a bias K-step (128 rows of (1, 1, 0, ..., 0), K = 16,
+// K-major core matrices) at shared-memory byte offset `off`; all threads of
+// the block take part.
+BL_DEV void init_ones(uint8_t *smem, uint32_t off, int tid, int nthreads) {
+  for (int i = tid; i < 128 * 16; i += nthreads) {
+    const int m = i / 16, k = i % 16;
+    *reinterpret_cast<__nv_bfloat16 *>(smem + off + img_off(m, k, 16)) =
+        __float2bfloat16_rn(k < 2 ? 1.0f : 0.0f);
+  }
+}
+
+// One thread: bulk-copy the whole weight image to shared memory at `sbase`,
+// completing MLP_IMG_BYTES of transactions on mbarrier `bar`.
+BL_DEV void load_weights(uint32_t sbase, const uint8_t *img, uint32_t bar) {
+  tc::mbar_expect_tx(bar, MLP_IMG_BYTES);
+  tc::bulk_g2s(sbase + OFF_W0, img + OFF_W0, MLP_IMG_W0, bar);
+  for (int l = 0; l < 3; ++l)
+    tc::bulk_g2s(sbase + OFF_W1 + l * MLP_IMG_WH, img + OFF_W1 + l * MLP_IMG_WH, MLP_IMG_WH, bar);
+  tc::bulk_g2s(sbase + OFF_W4, img + OFF_W4, MLP_IMG_W4 + 3 * MLP_IMG_BH + MLP_IMG_B4, bar);
+}
+
+// FP64 normalisation constants as double-float pairs (hi, lo).
+inline MlpNormF norm_pairs(const MlpNorm &n64) {
+  MlpNormF n;
+  auto split = [](double v, float *hl) {
+    hl[0] = (float)v;
+    hl[1] = (float)(v - (double)hl[0]);
+  };
+  for (int c = 0; c < 6; ++c) {
+    split(n64.mu_in[c], n.mu_in[c]);
+    split(n64.inv_sd_in[c], n.inv_sd_in[c]);
+    split(n64.mu_out[c], n.mu_out[c]);
+    split(n64.sd_out[c], n.sd_out[c]);
+  }
+  return n;
+}
+
+}  // namespace mlp
+}  // namespace bl

@@ -36,15 +36,13 @@
 //    carries about 44 bits, i.e. FP64-grade constants and rounding, on the
 //    FP32 pipes. A slot's next inputs are loaded from HBM while the current
 //    tile is in the network.
-#include <cuda_bf16.h>
-
-#include "common.cuh"
-#include "internal.h"
-#include "tc.cuh"
+#include "mlp_common.cuh"
 
 namespace bl {
 
 namespace {
+
+using namespace mlp;
 
 constexpr int SLOTS = 3;
 constexpr int WG_PER_SLOT = 2;                     // epilogue warpgroups per slot
@@ -53,11 +51,6 @@ constexpr int CHUNK = 16;                          // accumulator columns per tc
 constexpr int EPI_THREADS = 128 * WG_PER_SLOT * SLOTS;
 constexpr int THREADS = EPI_THREADS + 32;          // + the MMA warp
 constexpr int MMA_WARP = EPI_THREADS / 32;
-constexpr uint32_t OFF_W0 = 0;
-constexpr uint32_t OFF_W1 = OFF_W0 + MLP_IMG_W0;
-constexpr uint32_t OFF_W4 = OFF_W1 + 3 * MLP_IMG_WH;
-constexpr uint32_t OFF_B1 = OFF_W4 + MLP_IMG_W4;
-constexpr uint32_t OFF_B4 = OFF_B1 + 3 * MLP_IMG_BH;
 constexpr uint32_t ACT_BYTES = 128 * 128 * 2;      // one slot's BF16 activations
 constexpr uint32_t OFF_ACT = (MLP_IMG_BYTES + 1023) / 1024 * 1024;
 constexpr uint32_t OFF_ONES = OFF_ACT + SLOTS * ACT_BYTES;  // 128 x 16 BF16 A matrix
@@ -70,16 +63,6 @@ static_assert(SMEM_BYTES > 114 * 1024, "one CTA per SM (it owns all tensor memor
 // Tensor memory: 128 FP32 accumulator columns per slot.
 constexpr uint32_t TMEM_COLS = 512;
 static_assert(128 * SLOTS <= TMEM_COLS, "tensor memory budget");
-
-constexpr float GELU_C0 = 0.7978845608028654f;               // sqrt(2/pi)
-constexpr float GELU_C1 = 0.7978845608028654f * 0.044715f;
-
-// Byte offset of element (n, k) of an [N x K] K-major BF16 block in the
-// no-swizzle core-matrix layout: 8x8 core matrices of 128 contiguous bytes,
-// adjacent along K at 128 bytes, adjacent along N at (K/8)*128 bytes.
-__host__ __device__ inline uint32_t img_off(int n, int k, int K) {
-  return (uint32_t)((n >> 3) * (K / 8) * 128 + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2);
-}
 
 // Two hidden pre-activations (FP32 accumulators r0, r1, bias included) ->
 // packed BF16 pair of 2*GELU: u = x (c0 + c1 x^2) in FP32x2, tanh.approx.f32,
@@ -118,36 +101,6 @@ BL_DEV void gelu_chunk(const uint32_t (&r)[CH], uint32_t row, int f0) {
   }
 }
 
-// Double-float helpers: a value v is carried as hi + lo (FP32 each).
-BL_DEV void two_sum(float a, float b, float &s, float &e) {
-  s = a + b;
-  const float bp = s - a;
-  e = (a - (s - bp)) + (b - bp);
-}
-
-// (z - mu) * inv with mu = mh + ml and inv = ih + il, rounded to FP32.
-BL_DEV float df_normalise(float z, float mh, float ml, float ih, float il) {
-  float dh, dl;
-  two_sum(z, -mh, dh, dl);
-  dl -= ml;
-  const float p = dh * ih;
-  const float pe = fmaf(dh, ih, -p);
-  return p + (pe + fmaf(dh, il, dl * ih));
-}
-
-// y * sd + mu with sd = sh + sl and mu = mh + ml, rounded to FP32.
-BL_DEV float df_affine(float y, float sh, float sl, float mh, float ml) {
-  const float p = y * sh;
-  const float pe = fmaf(y, sh, -p);
-  float s, se;
-  two_sum(p, mh, s, se);
-  return s + (se + pe + fmaf(y, sl, ml));
-}
-
-BL_DEV void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
 // Registers: the 4 sub-partitions of the SM each hold a quarter of the 64K
 // registers, and warp w runs on sub-partition w % 4, so the MMA warp makes
 // sub-partition 0 host one warp more than the others.
@@ -179,23 +132,13 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
   // constant A operand of the bias step: rows of (1, 1, 0, ..., 0), K-major
   // core matrices (8 rows x 16 bytes, K chunks 128 bytes apart, row groups
   // 256 bytes apart)
-  for (int i = tid; i < 128 * 16; i += THREADS) {
-    const int m = i / 16, k = i % 16;
-    *reinterpret_cast<__nv_bfloat16 *>(smem + OFF_ONES + img_off(m, k, 16)) =
-        __float2bfloat16_rn(k < 2 ? 1.0f : 0.0f);
-  }
+  init_ones(smem, OFF_ONES, tid, THREADS);
   tc::fence_proxy_async();
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = *tslot;
-  if (tid == 0) {
-    tc::mbar_expect_tx(bar_w, MLP_IMG_BYTES);
-    tc::bulk_g2s(sbase + OFF_W0, img + OFF_W0, MLP_IMG_W0, bar_w);
-    for (int l = 0; l < 3; ++l)
-      tc::bulk_g2s(sbase + OFF_W1 + l * MLP_IMG_WH, img + OFF_W1 + l * MLP_IMG_WH, MLP_IMG_WH, bar_w);
-    tc::bulk_g2s(sbase + OFF_W4, img + OFF_W4, MLP_IMG_W4 + 3 * MLP_IMG_BH + MLP_IMG_B4, bar_w);
-  }
+  if (tid == 0) load_weights(sbase, img, bar_w);
 
   if (warp == MMA_WARP) {
     // ------------------------------------------------------------ MMA warp
@@ -214,7 +157,6 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
       const uint64_t d_w0 = tc::sdesc(sbase + OFF_W0, 128, 256);
       // layers 1..4: W1, W2, W3, W4 are MLP_IMG_WH bytes apart, and so are the
       // bias blocks B1..B4 at MLP_IMG_BH (the descriptor address is in 16 B units)
-      static_assert(OFF_W4 == OFF_W1 + 3 * MLP_IMG_WH && OFF_B4 == OFF_B1 + 3 * MLP_IMG_BH, "image");
       const uint64_t d_w1 = tc::sdesc(sbase + OFF_W1, 128, 2048);
       const uint64_t d_b1 = tc::sdesc(sbase + OFF_B1, 128, 256);
       // activation buffers: K = 16 layout for the input (layer 0), K = 128 after
@@ -525,21 +467,10 @@ cudaError_t launch_mlp_pack(const float *params, uint8_t *img, float *bias, floa
   return cudaGetLastError();
 }
 
-static void split_df(double v, float *hl) {
-  hl[0] = (float)v;
-  hl[1] = (float)(v - (double)hl[0]);
-}
-
 cudaError_t launch_mlp_forward(Soa<float> z, int64_t n, const uint8_t *img, const MlpNorm &nrm64,
                                int num_sms, unsigned *err, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  MlpNormF nrm;
-  for (int c = 0; c < 6; ++c) {
-    split_df(nrm64.mu_in[c], nrm.mu_in[c]);
-    split_df(nrm64.inv_sd_in[c], nrm.inv_sd_in[c]);
-    split_df(nrm64.mu_out[c], nrm.mu_out[c]);
-    split_df(nrm64.sd_out[c], nrm.sd_out[c]);
-  }
+  const MlpNormF nrm = mlp::norm_pairs(nrm64);
   const int64_t ntiles = (n + 127) / 128;
   int64_t grid = (ntiles + SLOTS - 1) / SLOTS;
   if (grid > num_sms) grid = num_sms;

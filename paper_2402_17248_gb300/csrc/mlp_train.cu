@@ -31,7 +31,7 @@ __host__ __device__ constexpr int boff(int l) {
 constexpr float C0 = 0.7978845608028654f;
 constexpr float C1 = 0.7978845608028654f * 0.044715f;
 
-enum Mode { MODE_TRAIN = 0, MODE_VJP = 1, MODE_LOSS = 2 };
+enum Mode { MODE_TRAIN = 0, MODE_LOSS = 1 };
 
 BL_DEV float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
@@ -54,13 +54,13 @@ struct Smem {
   double loss[NT / 32];
 };
 
-// Inputs zin (and targets zout, or upstream adjoints lam in VJP mode) are
+// Inputs zin and targets zout are
 // six coordinate arrays indexed by column idx[s] (or s when idx is NULL).
 template <int MODE>
 __global__ void __launch_bounds__(NT)
 mlp_grad_kernel(Soa<float> zin, Soa<float> zout, const int64_t *__restrict__ idx, int64_t count,
                 const float *__restrict__ wt, const float *__restrict__ wn, MlpNorm nrm,
-                float *__restrict__ part, double *__restrict__ loss_part, Soa<float> lam,
+                float *__restrict__ part, double *__restrict__ loss_part,
                 double inv_count6) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
@@ -130,30 +130,24 @@ mlp_grad_kernel(Soa<float> zin, Soa<float> zout, const int64_t *__restrict__ idx
     float d = 0.f;
     if (s < ns) {
       const int64_t col = idx ? idx[s0 + s] : s0 + s;
-      if (MODE == MODE_VJP) {
-        d = (float)((double)lam.c[o][col] * nrm.sd_out[o]);
-      } else {
-        const float tgt = (float)(((double)zout.c[o][col] - nrm.mu_out[o]) / nrm.sd_out[o]);
-        const float diff = acc - tgt;
-        lsum = (double)diff * (double)diff;
-        d = (float)(2.0 * (double)diff * inv_count6);
-      }
+      const float tgt = (float)(((double)zout.c[o][col] - nrm.mu_out[o]) / nrm.sd_out[o]);
+      const float diff = acc - tgt;
+      lsum = (double)diff * (double)diff;
+      d = (float)(2.0 * (double)diff * inv_count6);
     }
     sm.d4[s][o] = d;
   }
-  if (MODE != MODE_VJP) {
-    lsum = warp_sum(lsum);
-    if ((tid & 31) == 0) sm.loss[tid >> 5] = lsum;
-  }
+  lsum = warp_sum(lsum);
+  if ((tid & 31) == 0) sm.loss[tid >> 5] = lsum;
   __syncthreads();
-  if (MODE != MODE_VJP && tid == 0) {
+  if (tid == 0) {
     double t = 0.0;
     for (int w = 0; w < NT / 32; ++w) t += sm.loss[w];
     loss_part[blockIdx.x] = t;
   }
   if (MODE == MODE_LOSS) return;
 
-  float *P = (MODE == MODE_TRAIN) ? part + (int64_t)blockIdx.x * MLP_PSTRIDE : nullptr;
+  float *P = part + (int64_t)blockIdx.x * MLP_PSTRIDE;
 
   // ---- layer 4 backward: dW4, db4; dh_4 = W4^T d4
   if (MODE == MODE_TRAIN) {
@@ -245,16 +239,6 @@ mlp_grad_kernel(Soa<float> zin, Soa<float> zout, const int64_t *__restrict__ idx
     for (int s = 0; s < S; ++s) bsum += dj[s];
     P[boff(0) + tid] = bsum;
   }
-  if (MODE == MODE_VJP && tid < 6 * S) {
-    const int c = tid / S, s = tid % S;
-    if (s < ns) {
-      const float *W = wn + woff(0);  // [out j][in c]
-      float a = 0.f;
-      for (int j = 0; j < 128; ++j) a = fmaf(W[j * 6 + c], sm.d[s][j], a);
-      const int64_t col = idx ? idx[s0 + s] : s0 + s;
-      lam.c[c][col] = (float)((double)a * nrm.inv_sd_in[c]);
-    }
-  }
 }
 
 __global__ void __launch_bounds__(256)
@@ -299,7 +283,7 @@ __global__ void loss_finalize_kernel(const double *__restrict__ lp, int nblocks,
 template <int MODE>
 cudaError_t launch_grad_mode(Soa<float> zin, Soa<float> zout, const int64_t *idx, int64_t count,
                              const float *wt, const float *wn, const MlpNorm &nrm, float *part,
-                             double *loss_part, Soa<float> lam, cudaStream_t st) {
+                             double *loss_part, cudaStream_t st) {
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(mlp_grad_kernel<MODE>,
@@ -312,7 +296,7 @@ cudaError_t launch_grad_mode(Soa<float> zin, Soa<float> zout, const int64_t *idx
   const int64_t nb = (count + S - 1) / S;
   const double inv = 1.0 / (6.0 * (double)count);
   mlp_grad_kernel<MODE><<<(unsigned)nb, NT, sizeof(Smem), st>>>(zin, zout, idx, count, wt, wn,
-                                                                nrm, part, loss_part, lam, inv);
+                                                                nrm, part, loss_part, inv);
   return cudaGetLastError();
 }
 
@@ -331,9 +315,8 @@ cudaError_t launch_mlp_grad(const float *in, const float *out, int64_t ld, const
                             float *partials, double *loss_partials, int *nblocks_out,
                             cudaStream_t st) {
   *nblocks_out = mlp_grad_blocks(batch);
-  Soa<float> none{};
   return launch_grad_mode<MODE_TRAIN>(cols6(in, ld), cols6(out, ld), idx, batch, wt, wn, nrm,
-                                      partials, loss_partials, none, st);
+                                      partials, loss_partials, st);
 }
 
 cudaError_t launch_mlp_reduce_adam(const float *partials, int nblocks, const double *loss_partials,
@@ -354,9 +337,8 @@ cudaError_t launch_mlp_loss(const float *in, const float *out, int64_t ld, const
                             int64_t count, const float *wt, const float *wn, const MlpNorm &nrm,
                             double *loss_partials, int *nblocks_out, cudaStream_t st) {
   *nblocks_out = mlp_grad_blocks(count);
-  Soa<float> none{};
   return launch_grad_mode<MODE_LOSS>(cols6(in, ld), cols6(out, ld), idx, count, wt, wn, nrm,
-                                     nullptr, loss_partials, none, st);
+                                     nullptr, loss_partials, st);
 }
 
 cudaError_t launch_loss_finalize(const double *loss_partials, int nblocks, int64_t count,
@@ -364,13 +346,6 @@ cudaError_t launch_loss_finalize(const double *loss_partials, int nblocks, int64
   loss_finalize_kernel<<<1, 256, 0, st>>>(loss_partials, nblocks, 1.0 / (6.0 * (double)count),
                                           loss_out);
   return cudaGetLastError();
-}
-
-cudaError_t launch_mlp_vjp(Soa<float> zin, Soa<float> lam, int64_t n, const float *wt,
-                           const float *wn, const MlpNorm &nrm, cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
-  Soa<float> none{};
-  return launch_grad_mode<MODE_VJP>(zin, none, nullptr, n, wt, wn, nrm, nullptr, nullptr, lam, st);
 }
 
 }  // namespace bl

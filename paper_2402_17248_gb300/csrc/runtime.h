@@ -45,6 +45,7 @@ struct DevCtx {
   bool arch_ok = false;
   unsigned *err_word = nullptr;  // device word for BL_DEVERR_* flags
   bool mlp_configured = false;
+  bool mlp_vjp_configured = false;
 };
 // Context of the current device; checks the architecture (sm_103) once.
 bl_status current_ctx(DevCtx **out);
