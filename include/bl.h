@@ -88,7 +88,7 @@ typedef struct {
   double gamma_ref;
 } bl_bunch;
 
-typedef enum { BL_DRIFT = 0, BL_QUAD = 1, BL_SBEND = 2, BL_PLASMA = 3 } bl_kind;
+typedef enum { BL_DRIFT = 0, BL_QUAD = 1, BL_SBEND = 2, BL_PLASMA = 3, BL_PLASMA_LENS = 4 } bl_kind;
 
 struct bl_surrogate_s;
 typedef struct bl_surrogate_s bl_surrogate;
@@ -103,10 +103,16 @@ typedef struct bl_lattice_s bl_lattice;
  *   BL_PLASMA: L [m], nsteps RK4 steps, n0_cm3 plasma density [1/cm^3],
  *              E0_Vpm wake amplitude [V/m], phi0 reference phase [rad];
  *              surrogate: trained stage surrogate, or NULL for the RK4 push.
+ *   BL_PLASMA_LENS: L [m], k [1/m^2] focusing both planes alike (k > 0
+ *              focuses): the linear map of an active plasma lens, whose
+ *              azimuthal field gradient g = dB/dr [T/m] gives k = e g / p_ref
+ *              (Sec. 4: plasma lenses between stages). per_bunch_k must be
+ *              NULL; lens strengths are not among the strengths that
+ *              bl_track_grad differentiates.
  * The linear maps are the solutions of the linear equations of motion of
  * H = px^2/2 + py^2/2 + pt^2/(2 b^2 g^2) + h^2 x^2/2 + h x pt/b + k (x^2-y^2)/2
- * (h = angle/L in a bend); the paper (Sec. 1, Sec. 4) treats them as given
- * conventional elements. */
+ * (h = angle/L in a bend; k (x^2+y^2)/2 in a plasma lens); the paper (Sec. 1,
+ * Sec. 4) treats them as given conventional elements. */
 typedef struct {
   int32_t kind;
   int32_t nsteps;
@@ -190,6 +196,16 @@ bl_status bl_apply_linear(bl_bunch *bunch, const double *M, int32_t per_bunch,
  * a deviation form relative to the FP64 reference trajectory; FP64 bunches in
  * FP64. */
 bl_status bl_push_stage(bl_bunch *bunch, const bl_element *stage, bl_stream stream);
+
+/* FP64 transfer matrix of a run of linear elements (host computation, no
+ * device work): M_out (36 doubles, row-major) = M_{n-1} ... M_1 M_0 for the
+ * elements' own strengths k (per_bunch_k is ignored) at reference
+ * gamma_ref > 1. Elements must be BL_DRIFT, BL_QUAD, BL_SBEND or
+ * BL_PLASMA_LENS; n = 0 gives the identity. The same matrices that bl_track
+ * composes into segment maps, exposed for matching and optimisation on the
+ * host (Sec. 4: the transport between stages is set from measured moments). */
+bl_status bl_segment_matrix(const bl_element *elements, int32_t n, double gamma_ref,
+                            double *M_out);
 
 /* FP64 on-axis reference particle through one stage (host computation).
  * Returns gamma at the exit given gamma at the entry. */

@@ -11,7 +11,11 @@ equations of motion of the Hamiltonian
         + h^2 x^2 / 2 + h x pt / beta + k (x^2 - y^2) / 2
 
 for a drift (h = k = 0), a quadrupole (h = 0; k > 0 focuses x) and a sector
-bend without edge focusing (k = 0, curvature h = angle / L).
+bend without edge focusing (k = 0, curvature h = angle / L). An active plasma
+lens (Sec. 4: the lenses between stages) focuses both planes alike: its
+Hamiltonian has k (x^2 + y^2) / 2 in place of the quadrupole's
+k (x^2 - y^2) / 2, with k = e g / p_ref for the azimuthal field gradient
+g = dB/dr.
 
 Parity: pinned by the matrix exponential of the generator of H (scipy
 expm), by symplecticity, emittance invariance and the chicane R56 closed form.
@@ -59,6 +63,25 @@ def quad(L, k, bg):
     M[2:4, 2:4] = _plane(L, -k)
     M[4, 5] = L / (bg * bg)
     return M
+
+
+def plasma_lens(L, k, bg):
+    """Active plasma lens of length L and strength k [1/m^2] in both planes."""
+    M = np.eye(6)
+    M[0:2, 0:2] = _plane(L, k)
+    M[2:4, 2:4] = _plane(L, k)
+    M[4, 5] = L / (bg * bg)
+    return M
+
+
+E_CHARGE = 1.602176634e-19      # C
+M_E = 9.1093837015e-31          # kg
+C_LIGHT = 299792458.0           # m/s
+
+
+def lens_k_from_gradient(grad_T_per_m, bg):
+    """k = e g / p_ref with p_ref = bg m_e c."""
+    return E_CHARGE * grad_T_per_m / (bg * M_E * C_LIGHT)
 
 
 def _dplane_dk(L, k):
@@ -120,6 +143,8 @@ def element_matrix(e, bg):
         return quad(e["L"], e["k"], bg)
     if kind == "sbend":
         return sbend(e["L"], e["angle"], bg)
+    if kind == "plasma_lens":
+        return plasma_lens(e["L"], e["k"], bg)
     raise ValueError("not a linear element: %r" % kind)
 
 
@@ -133,10 +158,10 @@ def generator(e, bg):
     A[0, 1] = 1.0
     A[2, 3] = 1.0
     A[4, 5] = 1.0 / (bg * bg)
-    k = e.get("k", 0.0) if e["kind"] == "quad" else 0.0
+    k = e.get("k", 0.0) if e["kind"] in ("quad", "plasma_lens") else 0.0
     h = e["angle"] / e["L"] if e["kind"] == "sbend" else 0.0
     A[1, 0] = -(h * h + k)
-    A[3, 2] = k
+    A[3, 2] = -k if e["kind"] == "plasma_lens" else k
     A[1, 5] = -h / b
     A[4, 0] = h / b
     return A

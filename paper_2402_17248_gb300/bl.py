@@ -14,11 +14,12 @@ LIB_PATH = os.path.join(_HERE, "libbl.so")
 BL_OK, BL_ERR_INVALID_ARG, BL_ERR_CUDA, BL_ERR_OOM = 0, 1, 2, 3
 BL_ERR_UNSUPPORTED_ARCH, BL_ERR_NONFINITE, BL_ERR_TIMEOUT, BL_ERR_STATE = 4, 5, 6, 7
 BL_F32, BL_F64 = 0, 1
-BL_DRIFT, BL_QUAD, BL_SBEND, BL_PLASMA = 0, 1, 2, 3
+BL_DRIFT, BL_QUAD, BL_SBEND, BL_PLASMA, BL_PLASMA_LENS = 0, 1, 2, 3, 4
 BL_OBJ_EPS_N_X, BL_OBJ_SIGMA_X, BL_OBJ_EPS_N_Y, BL_OBJ_SIGMA_Y = 0, 1, 2, 3
 BL_MLP_NPARAM = 51206
 OBJECTIVES = {"eps_n_x": 0, "sigma_x": 1, "eps_n_y": 2, "sigma_y": 3}
-KINDS = {"drift": BL_DRIFT, "quad": BL_QUAD, "sbend": BL_SBEND, "plasma": BL_PLASMA}
+KINDS = {"drift": BL_DRIFT, "quad": BL_QUAD, "sbend": BL_SBEND, "plasma": BL_PLASMA,
+         "plasma_lens": BL_PLASMA_LENS}
 WIDTHS = (6, 128, 128, 128, 128, 6)
 
 
@@ -66,6 +67,7 @@ _SIGS = {
     "bl_apply_linear": ([_P, _P, _I32, _P], C.c_int),
     "bl_push_stage": ([_P, _P, _P], C.c_int),
     "bl_reference_exit": ([_P, _D, _P], C.c_int),
+    "bl_segment_matrix": ([_P, _I32, _D, _P], C.c_int),
     "bl_beam_quantities": ([_P, _D, _P], C.c_int),
     "bl_surrogate_create": ([_P, _P], C.c_int),
     "bl_surrogate_destroy": ([_P], C.c_int),
@@ -255,6 +257,14 @@ def bl_reference_exit(stage, gamma_in):
     g = C.c_double()
     _check(lib().bl_reference_exit(arr, float(gamma_in), C.byref(g)))
     return g.value
+
+
+def bl_segment_matrix(elements, gamma_ref):
+    """FP64 6x6 transfer matrix of a run of linear elements (host)."""
+    arr, keep = make_elements(elements) if elements else (None, [])
+    M = np.zeros((6, 6))
+    _check(lib().bl_segment_matrix(arr, len(elements), float(gamma_ref), M.ctypes.data))
+    return M
 
 
 BEAM_QUANTITIES = ("eps_n_x", "eps_n_y", "sigma_x", "sigma_y", "mean_gamma", "rel_energy_spread")

@@ -153,9 +153,13 @@ bl_status bl_lattice_create(const bl_element *elements, int32_t n_elements, int3
   L->n_bunch_k = 0;
   for (int i = 0; i < n_elements; ++i) {
     const bl_element &e = elements[i];
-    BL_CHECK(e.kind >= BL_DRIFT && e.kind <= BL_PLASMA, "unknown element kind");
+    BL_CHECK(e.kind >= BL_DRIFT && e.kind <= BL_PLASMA_LENS, "unknown element kind");
     BL_CHECK(std::isfinite(e.L) && e.L >= 0.0, "element length must be finite and >= 0");
     if (e.kind == BL_QUAD) BL_CHECK(std::isfinite(e.k), "quad strength must be finite");
+    if (e.kind == BL_PLASMA_LENS) {
+      BL_CHECK(std::isfinite(e.k), "plasma lens strength must be finite");
+      BL_CHECK(!e.per_bunch_k, "plasma lenses take no per-bunch strengths");
+    }
     if (e.kind == BL_SBEND) {
       BL_CHECK(std::isfinite(e.angle), "bend angle must be finite");
       BL_CHECK(e.angle == 0.0 || e.L > 0.0, "a bend with an angle needs L > 0");
@@ -190,6 +194,27 @@ bl_status bl_lattice_create(const bl_element *elements, int32_t n_elements, int3
 
 bl_status bl_lattice_destroy(bl_lattice *lat) {
   delete lat;
+  return BL_OK;
+}
+
+bl_status bl_segment_matrix(const bl_element *elements, int32_t n, double gamma_ref,
+                            double *M_out) {
+  BL_CHECK(M_out, "M_out is NULL");
+  BL_CHECK(n >= 0 && (n == 0 || elements), "elements is NULL");
+  BL_CHECK(std::isfinite(gamma_ref) && gamma_ref > 1.0, "gamma_ref must be finite and > 1");
+  const double bg = std::sqrt(gamma_ref * gamma_ref - 1.0);
+  Mat6 M = mat_identity();
+  for (int i = 0; i < n; ++i) {
+    const bl_element &e = elements[i];
+    BL_CHECK(e.kind == BL_DRIFT || e.kind == BL_QUAD || e.kind == BL_SBEND ||
+                 e.kind == BL_PLASMA_LENS,
+             "bl_segment_matrix takes linear elements only");
+    BL_CHECK(std::isfinite(e.L) && e.L >= 0.0, "element length must be finite and >= 0");
+    BL_CHECK(std::isfinite(e.k) && std::isfinite(e.angle), "element strengths must be finite");
+    BL_CHECK(e.kind != BL_SBEND || e.angle == 0.0 || e.L > 0.0, "a bend with an angle needs L > 0");
+    M = mat_mul(element_matrix(e, e.k, bg), M);
+  }
+  for (int i = 0; i < 36; ++i) M_out[i] = M[i];
   return BL_OK;
 }
 

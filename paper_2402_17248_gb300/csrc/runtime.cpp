@@ -150,6 +150,12 @@ Mat6 element_matrix(const bl_element &e, double k, double bg) {
     M[0] = a[0]; M[1] = a[1]; M[6] = a[2]; M[7] = a[3];
     M[14] = b[0]; M[15] = b[1]; M[20] = b[2]; M[21] = b[3];
     M[4 * 6 + 5] = L / (bg * bg);
+  } else if (e.kind == BL_PLASMA_LENS) {
+    double a[4];
+    plane(L, k, a);
+    M[0] = a[0]; M[1] = a[1]; M[6] = a[2]; M[7] = a[3];
+    M[14] = a[0]; M[15] = a[1]; M[20] = a[2]; M[21] = a[3];
+    M[4 * 6 + 5] = L / (bg * bg);
   } else if (e.kind == BL_SBEND) {
     const double th = e.angle, h = th / L, beta = bg / std::sqrt(1.0 + bg * bg);
     const double C = std::cos(th), S = std::sin(th);

@@ -118,3 +118,14 @@ def surrogate_beamline(elements, surrogates):
             i += 1
         out.append(e)
     return out
+
+
+def plasma_lens_k(gradient_T_per_m, gamma_ref):
+    """Focusing strength [1/m^2] of an active plasma lens with azimuthal field
+    gradient g = dB/dr [T/m] for the reference momentum: k = e g / p_ref,
+    p_ref = (beta gamma)_ref m_e c (CODATA 2018 constants)."""
+    e = 1.602176634e-19
+    me_c = 9.1093837015e-31 * 299792458.0
+    bg = (gamma_ref * gamma_ref - 1.0) ** 0.5
+    return e * gradient_T_per_m / (bg * me_c)
+

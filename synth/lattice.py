@@ -37,6 +37,10 @@ def sbend(L, angle):
     return {"kind": "sbend", "L": L, "angle": angle}
 
 
+def plasma_lens(L, k):
+    return {"kind": "plasma_lens", "L": L, "k": k}
+
+
 def single_stage_transport(nsteps=200):
     """One plasma stage, then drift 0.5 m, four 0.1 m quads (k = +-50), drift 0.5 m."""
     return [plasma(nsteps), drift(0.5), quad(0.1, 50.0), quad(0.1, -50.0),

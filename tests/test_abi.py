@@ -66,6 +66,13 @@ def test_lattice_create_counts_and_validation():
         bl.Lattice([{"kind": "quad", "L": 0.1, "k": 1.0, "per_bunch_k": [1.0, 2.0]}])
     with pytest.raises(bl.BlError):
         bl.bl_reference_exit(lattice.plasma(10), 0.5)
+    # plasma lenses: a linear element, not a differentiated strength, no per-bunch k
+    L = bl.Lattice([lattice.drift(0.1), lattice.plasma_lens(0.03, 2000.0), lattice.quad(0.1, 5.0)])
+    assert L.num_elements == 3 and L.num_quads == 1
+    with pytest.raises(bl.BlError):
+        bl.Lattice([{"kind": "plasma_lens", "L": 0.03, "k": 1.0, "per_bunch_k": [1.0]}], n_bunch_k=1)
+    with pytest.raises(bl.BlError):
+        bl.Lattice([{"kind": "plasma_lens", "L": 0.03, "k": float("inf")}])
 
 
 def test_per_bunch_lattice():

@@ -192,3 +192,31 @@ def test_track_two_stage_beamline_fp32():
             worst = max(worst, abs(dg[k] / dw[k] - 1))
     print("fp32 two-stage beamline worst relative moment error:", worst)
     assert worst < 1e-5
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_track_plasma_lens_section(dtype):
+    """Stage, then drift + active plasma lens (k from a field gradient of
+    3 kT/m) + drift + defocusing lens + drift: particles and moments after
+    every element against the oracle (the lens map comes from the library's
+    own element matrices)."""
+    from paper_2402_17248_gb300 import bl, workflow
+    z, g = _bunch(20001, seed=8)
+    if dtype == "f32":
+        z = as_f32(z)
+    st = lattice.plasma(200)
+    g1 = bl.bl_reference_exit(st, g)
+    k_lens = workflow.plasma_lens_k(3000.0, g1)
+    els = [st, lattice.drift(0.05), lattice.plasma_lens(0.03, k_lens), lattice.drift(0.1),
+           lattice.plasma_lens(0.01, -0.3 * k_lens), lattice.drift(0.2)]
+    b = to_bunch(z, g, dtype=dtype)
+    mom, nonfin = bl.bl_track(b, bl.Lattice(els))
+    assert nonfin == 0
+    zo, go, snaps = beamline.track(z, g, els)
+    tol = 1e-10 if dtype == "f64" else 1e-5
+    for e, (want, gr) in enumerate(snaps):
+        _cmp_moments(mom[e][0], want, tol)
+    got = from_bunch(b)
+    ptol = 1e-10 if dtype == "f64" else 1e-3  # FP32: 200-step stage, as the pusher test
+    for a, w in zip(got, zo):
+        assert np.max(np.abs(a - w)) <= ptol * np.std(w)

@@ -23,6 +23,9 @@ ELEMS = [
     {"kind": "sbend", "L": 0.2, "angle": 1e-3},
     {"kind": "sbend", "L": 0.2, "angle": -1e-3},
     {"kind": "sbend", "L": 1.0, "angle": 0.3},
+    {"kind": "plasma_lens", "L": 0.03, "k": 2000.0},
+    {"kind": "plasma_lens", "L": 0.03, "k": -500.0},
+    {"kind": "plasma_lens", "L": 0.03, "k": 1e-9},
 ]
 
 
@@ -91,3 +94,42 @@ def test_chicane_r56_small_angle():
     assert abs(r56 / closed - 1) < 10 * th * th
     # dispersion closes to third order in the angle
     assert abs(M[0, 5]) < 10 * th ** 3 * Ltot and abs(M[1, 5]) < 10 * th ** 3
+
+
+def _rotation(theta):
+    """Rotation by theta about the beam axis, acting on (x, y) and (px, py)."""
+    c, s_ = math.cos(theta), math.sin(theta)
+    R = np.eye(6)
+    for a, b in ((0, 2), (1, 3)):
+        R[a, a], R[a, b], R[b, a], R[b, b] = c, -s_, s_, c
+    return R
+
+
+def test_plasma_lens_is_round():
+    """A plasma lens focuses both planes alike, so it commutes with rotations
+    about the axis; a quadrupole of the same strength does not."""
+    bg = BG[0]
+    R = _rotation(0.37)
+    Ml = maps.plasma_lens(0.03, 2000.0, bg)
+    Mq = maps.quad(0.03, 2000.0, bg)
+    assert np.max(np.abs(R @ Ml @ R.T - Ml)) < 1e-14
+    assert np.max(np.abs(R @ Mq @ R.T - Mq)) > 1e-2
+
+
+def test_plasma_lens_thin_limit_and_drift_limit():
+    bg = BG[0]
+    f = 0.25  # focal length [m]
+    for L in (1e-3, 1e-4):
+        M = maps.plasma_lens(L, 1.0 / (f * L), bg)
+        for a in (0, 2):
+            assert abs(M[a + 1, a] + 1.0 / f) < 2.0 * L / f ** 2  # -1/f (1 - O(L/f))
+            assert abs(M[a, a] - 1.0) < L / f
+    D = maps.drift(0.03, bg)
+    assert np.array_equal(maps.plasma_lens(0.03, 0.0, bg), D)
+
+
+def test_lens_strength_from_gradient():
+    """k = e g / p: at p = 1 GeV/c the magnetic rigidity is 1e9 / c T m."""
+    bg = 1000.0 / 0.51099895000
+    brho = 1e9 / 299792458.0
+    assert abs(maps.lens_k_from_gradient(1000.0, bg) / (1000.0 / brho) - 1) < 1e-9
