@@ -14,6 +14,11 @@ y = y~ sigma_out + mu_out. Loss: MSE(x, y) = (1/(N n)) sum (x_ij - y_ij)^2
 
 Weights are stored as W[l] with shape (out, in), as in Eq. L_i(v) = A_i v + b_i.
 
+The paper's own networks (Sec. 4.2: five hidden layers of 900 units for the
+first stages, three of 700 for the later ones) use PReLU,
+prelu(x) = max(x, 0) + a min(x, 0) with one learned slope a per layer (the
+single-parameter form; reading). `forward(..., slopes=[a_0, ...])` selects it.
+
 Optional BF16 emulation rounds the network input and every hidden activation
 to bfloat16 (round to nearest even) at the points where a BF16 datapath
 stores them; all sums stay FP64.
@@ -54,8 +59,13 @@ def gelu_grad(x):
     return 0.5 * (1.0 + t) + 0.5 * x * (1.0 - t * t) * du
 
 
-def forward(Ws, bs, X, bf16=False, keep=False):
-    """X: (N, n_in) normalised inputs. Returns outputs (N, n_out) [, cache]."""
+def prelu(x, a):
+    return np.where(x > 0.0, x, a * x)
+
+
+def forward(Ws, bs, X, bf16=False, keep=False, slopes=None):
+    """X: (N, n_in) normalised inputs. Returns outputs (N, n_out) [, cache].
+    slopes: None for GELU, else one PReLU slope per hidden layer."""
     h = np.asarray(X, dtype=np.float64)
     if bf16:
         h = bf16_round(h)
@@ -65,7 +75,7 @@ def forward(Ws, bs, X, bf16=False, keep=False):
         a = h @ Ws[l].T + bs[l]
         if l < nl - 1:
             pre.append(a)
-            h = gelu(a)
+            h = gelu(a) if slopes is None else prelu(a, slopes[l])
             if bf16:
                 h = bf16_round(h)
             acts.append(h)
@@ -135,7 +145,8 @@ class Adam:
 class Surrogate:
     """A trained stage surrogate: weights plus FP64 normalisation constants."""
 
-    def __init__(self, Ws, bs, mu_in, sd_in, mu_out, sd_out):
+    def __init__(self, Ws, bs, mu_in, sd_in, mu_out, sd_out, slopes=None):
+        self.slopes = None if slopes is None else [float(a) for a in slopes]
         self.Ws = [np.asarray(W, dtype=np.float64) for W in Ws]
         self.bs = [np.asarray(b, dtype=np.float64) for b in bs]
         self.mu_in = np.asarray(mu_in, dtype=np.float64)
@@ -146,6 +157,6 @@ class Surrogate:
     def apply(self, z, bf16=False):
         """Map relative coordinates at stage entry to those at stage exit."""
         X = (np.stack([np.asarray(c, dtype=np.float64) for c in z], axis=1) - self.mu_in) / self.sd_in
-        Yn = forward(self.Ws, self.bs, X, bf16=bf16)
+        Yn = forward(self.Ws, self.bs, X, bf16=bf16, slopes=self.slopes)
         Y = Yn * self.sd_out + self.mu_out
         return [Y[:, j].copy() for j in range(6)]

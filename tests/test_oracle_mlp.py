@@ -140,3 +140,31 @@ def test_adam_matches_torch_over_steps():
         tp.grad = torch.tensor(g)
         topt.step()
     assert np.max(np.abs(p[0] - tp.detach().numpy())) < 1e-14
+
+
+def test_prelu_network_matches_torch():
+    """The paper's PReLU networks (one slope per layer) against torch's prelu,
+    including a BF16-emulating pass whose rounding points torch reproduces
+    with explicit casts."""
+    Ws, bs = _net(widths=[6, 40, 40, 40, 6])
+    slopes = [0.25, -0.1, 0.6]
+    rng = np.random.default_rng(5)
+    X = rng.normal(size=(53, 6))
+    Y = mlp.forward(Ws, bs, X, slopes=slopes)
+    h = torch.tensor(X)
+    for l, (W, b) in enumerate(zip(Ws, bs)):
+        h = h @ torch.tensor(W).T + torch.tensor(b)
+        if l < len(Ws) - 1:
+            h = torch.nn.functional.prelu(h, torch.tensor([slopes[l]], dtype=torch.float64))
+    assert np.max(np.abs(Y - h.numpy())) < 1e-13
+    # BF16 emulation: round the input and every hidden activation
+    Yb = mlp.forward(Ws, bs, X, bf16=True, slopes=slopes)
+    h = torch.tensor(X).to(torch.bfloat16).double()
+    for l, (W, b) in enumerate(zip(Ws, bs)):
+        h = h @ torch.tensor(W).T + torch.tensor(b)
+        if l < len(Ws) - 1:
+            h = torch.nn.functional.prelu(h, torch.tensor([slopes[l]], dtype=torch.float64))
+            h = h.to(torch.bfloat16).double()
+    assert np.max(np.abs(Yb - h.numpy())) < 1e-13
+    # closed form on special values
+    assert np.array_equal(mlp.prelu(np.array([-2.0, 0.0, 3.0]), 0.25), np.array([-0.5, 0.0, 3.0]))
