@@ -228,6 +228,35 @@ typedef struct {
   const double *mu_in, *sd_in, *mu_out, *sd_out; /* 6 each */
 } bl_mlp_desc;
 
+/* ---- the paper's wide surrogate networks (Sec. 4.2) ----
+ * F = L_{n-1} o prelu o ... o prelu o L_0 with PReLU (one learned slope per
+ * hidden layer): widths[0] = widths[n_layers] = 6, hidden widths 1..4096
+ * (e.g. five layers of 900 or three of 700 units). Weights are rounded to
+ * BF16, activations are BF16 between layers, sums FP32; inputs and outputs
+ * are normalised as for bl_surrogate. Weights W[l] are host FP32 row-major
+ * [widths[l+1]][widths[l]], b[l] host FP32, slopes host FP32 (n_layers - 1).
+ * Hidden widths are padded on the device with zero weights to multiples of
+ * 64. */
+typedef struct {
+  int32_t n_layers;
+  const int32_t *widths;
+  const float *const *W;
+  const float *const *b;
+  const float *slopes;
+  const double *mu_in, *sd_in, *mu_out, *sd_out;
+} bl_wide_mlp_desc;
+
+struct bl_wide_mlp_s;
+typedef struct bl_wide_mlp_s bl_wide_mlp;
+
+bl_status bl_wide_mlp_create(const bl_wide_mlp_desc *desc, bl_wide_mlp **out);
+bl_status bl_wide_mlp_destroy(bl_wide_mlp *m);
+/* Apply the network to every particle of an FP32 bunch in place, `chunk`
+ * particles at a time (0: 2^21); the library keeps two activation buffers
+ * of chunk x (widest padded layer) BF16 values per stream. */
+bl_status bl_wide_mlp_apply(const bl_wide_mlp *m, bl_bunch *bunch, int64_t chunk,
+                            bl_stream stream);
+
 bl_status bl_surrogate_create(const bl_mlp_desc *desc, bl_surrogate **out);
 bl_status bl_surrogate_destroy(bl_surrogate *s);
 

@@ -49,6 +49,14 @@ class bl_mlp_desc(C.Structure):
                 ("mu_out", C.POINTER(C.c_double)), ("sd_out", C.POINTER(C.c_double))]
 
 
+class bl_wide_mlp_desc(C.Structure):
+    _fields_ = [("n_layers", C.c_int32), ("widths", C.POINTER(C.c_int32)),
+                ("W", C.POINTER(C.POINTER(C.c_float))), ("b", C.POINTER(C.POINTER(C.c_float))),
+                ("slopes", C.POINTER(C.c_float)),
+                ("mu_in", C.POINTER(C.c_double)), ("sd_in", C.POINTER(C.c_double)),
+                ("mu_out", C.POINTER(C.c_double)), ("sd_out", C.POINTER(C.c_double))]
+
+
 class bl_adam_cfg(C.Structure):
     _fields_ = [("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double),
                 ("eps", C.c_double)]
@@ -77,6 +85,9 @@ _SIGS = {
     "bl_surrogate_grad": ([_P, _P, _P, _I64, _P, _I64, _P, _P, _P], C.c_int),
     "bl_surrogate_loss": ([_P, _P, _P, _I64, _P, _I64, _P, _P], C.c_int),
     "bl_track_grad": ([_P, _P, _I32, _P, _P, _P], C.c_int),
+    "bl_wide_mlp_create": ([_P, _P], C.c_int),
+    "bl_wide_mlp_destroy": ([_P], C.c_int),
+    "bl_wide_mlp_apply": ([_P, _P, _I64, _P], C.c_int),
     "bl_last_error_message": ([], C.c_char_p),
     "bl_version": ([], C.c_char_p),
     "bl_poll_device_errors": ([], C.c_int),
@@ -311,6 +322,41 @@ class Surrogate:
         bp = (C.POINTER(C.c_float) * 5)(*[b.ctypes.data_as(C.POINTER(C.c_float)) for b in bs])
         _check(lib().bl_surrogate_get_params(self.handle, Wp, bp))
         return Ws, bs
+
+
+class WideSurrogate:
+    """bl_wide_mlp handle: the paper's PReLU networks of any widths
+    6 -> H ... H -> 6 (weights W[l] out x in, biases b[l], one slope per
+    hidden layer, FP64 normalisation constants)."""
+
+    def __init__(self, Ws, bs, slopes, mu_in, sd_in, mu_out, sd_out):
+        L = len(Ws)
+        Wf = [np.ascontiguousarray(W, dtype=np.float32) for W in Ws]
+        bf = [np.ascontiguousarray(b, dtype=np.float32) for b in bs]
+        sl = np.ascontiguousarray(slopes, dtype=np.float32)
+        nrm = [np.ascontiguousarray(v, dtype=np.float64) for v in (mu_in, sd_in, mu_out, sd_out)]
+        self.widths = [Wf[0].shape[1]] + [W.shape[0] for W in Wf]
+        widths = (C.c_int32 * (L + 1))(*self.widths)
+        Wp = (C.POINTER(C.c_float) * L)(*[w.ctypes.data_as(C.POINTER(C.c_float)) for w in Wf])
+        bp = (C.POINTER(C.c_float) * L)(*[b.ctypes.data_as(C.POINTER(C.c_float)) for b in bf])
+        d = bl_wide_mlp_desc()
+        d.n_layers = L
+        d.widths = widths
+        d.W = Wp
+        d.b = bp
+        d.slopes = sl.ctypes.data_as(C.POINTER(C.c_float))
+        d.mu_in, d.sd_in, d.mu_out, d.sd_out = [v.ctypes.data_as(C.POINTER(C.c_double)) for v in nrm]
+        self.handle = C.c_void_p()
+        _check(lib().bl_wide_mlp_create(C.byref(d), C.byref(self.handle)))
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.bl_wide_mlp_destroy(self.handle)
+            self.handle = None
+
+
+def bl_wide_mlp_apply(net, bunch, chunk=0, stream=None):
+    _check(lib().bl_wide_mlp_apply(net.handle, bunch.ref(), int(chunk), _stream(stream)))
 
 
 def bl_surrogate_create(Ws, bs, mu_in, sd_in, mu_out, sd_out):

@@ -85,6 +85,23 @@ cudaError_t launch_mlp_forward(Soa<float> z, int64_t n, const uint8_t *img, cons
                                int num_sms, unsigned *err, cudaStream_t st);
 cudaError_t mlp_forward_configure();
 
+// ---- wide PReLU networks (wide_mlp.cu) ----
+struct WideNet {
+  struct Layer {
+    uint8_t *W = nullptr;  // BF16 weights, tiled (see wide_weight_offset)
+    float *b = nullptr;    // FP32 bias, N_pad entries
+    float slope = 0.0f;    // PReLU slope (hidden layers)
+    int K_pad = 0, N_pad = 0;
+  };
+  std::vector<Layer> layers;
+  MlpNorm nrm{};
+};
+// Byte offset of weight (n, k) in a layer's tiled BF16 image.
+size_t wide_weight_offset(int n, int k, int N_pad);
+cudaError_t wide_mlp_configure();
+cudaError_t launch_wide_mlp(Soa<float> z, int64_t n, const WideNet &net, uint8_t *act0,
+                            uint8_t *act1, int num_sms, unsigned *err, cudaStream_t st);
+
 // Partial-gradient row stride (floats) of the training kernels, padded for
 // 16-byte aligned vector stores.
 constexpr int MLP_PSTRIDE = 51208;

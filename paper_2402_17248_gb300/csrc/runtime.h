@@ -46,6 +46,7 @@ struct DevCtx {
   unsigned *err_word = nullptr;  // device word for BL_DEVERR_* flags
   bool mlp_configured = false;
   bool mlp_vjp_configured = false;
+  bool wide_configured = false;
 };
 // Context of the current device; checks the architecture (sm_103) once.
 bl_status current_ctx(DevCtx **out);
@@ -53,7 +54,7 @@ bl_status current_ctx(DevCtx **out);
 // ---- workspaces ----
 enum WsSlot {
   WS_PARTIALS = 0, WS_MOMENTS, WS_NONFINITE, WS_TABLES, WS_MATS, WS_CENTERS, WS_LAMBDA,
-  WS_CKPT, WS_CROSS, WS_TRAIN, WS_LOSS, WS_COUNT
+  WS_CKPT, WS_CROSS, WS_TRAIN, WS_LOSS, WS_WIDE0, WS_WIDE1, WS_COUNT
 };
 struct Workspace {
   void *ptr[WS_COUNT] = {};
@@ -126,6 +127,12 @@ struct bl_surrogate_s {
   bl::MlpNorm nrm{};
   double mu_in[6], sd_in[6], mu_out[6], sd_out[6];
   int step = 0;
+};
+
+struct bl_wide_mlp_s {
+  int device = -1;
+  bl::WideNet net;
+  int max_width = 0;  // largest K_pad / N_pad of any layer
 };
 
 struct bl_lattice_s {
