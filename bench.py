@@ -63,6 +63,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the batched-bunch, adjoint and training side measurements")
+    p.add_argument("--paper-networks-only", action="store_true",
+                   help="time only the paper-shaped wide PReLU networks and print their JSON")
+    p.add_argument("--paper-particles", type=int, default=10_000_000)
     return p.parse_args()
 
 
@@ -176,7 +179,8 @@ def run_reference(args):
 def side_measurements(args, bl, workflow, lattice, surs, infos, z0, g, elements, dev):
     """Throughput of the other paths on the hot-path list, reported beside the
     headline (not part of it): surrogate training, the batched uneven-bunch
-    beamline with per-bunch quadrupoles and the adjoint."""
+    beamline with per-bunch quadrupoles, the adjoint and the paper's own wide
+    PReLU network shapes."""
     import torch
     from synth.bunch import random_quad_magnitudes, uneven_counts
     out = {}
@@ -273,7 +277,53 @@ def side_measurements(args, bl, workflow, lattice, surs, infos, z0, g, elements,
                       "timing": "host wall clock per bl_track_grad call (it returns host values)"}
     del za, za0, ba
     torch.cuda.empty_cache()
+
+    out["paper_networks"] = paper_networks(bl, args.paper_particles, g, dev)
+    torch.cuda.empty_cache()
     return out
+
+
+def paper_networks(bl, npw, g, dev):
+    """The paper's own surrogate shapes (Sec. 4.2): PReLU networks with five
+    hidden layers of 900 units and three of 700, random-init weights (the
+    timing does not depend on their values), on npw particles (1e7 in the
+    paper's timing, Sec. 4.3); the paper's A100 figures are context only."""
+    import torch
+    from synth.bunch import mlp_init
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    zw = [torch.randn(npw, device=dev, dtype=torch.float32) for _ in range(6)]
+    bw = bl.Bunch(zw, g)
+    one, zero = np.ones(6), np.zeros(6)
+    rows = []
+    for widths, paper_ns in (([6] + [900] * 5 + [6], 112.0), ([6] + [700] * 3 + [6], 49.4)):
+        Ws, bs = mlp_init(widths, 1)
+        net = bl.WideSurrogate(Ws, bs, [0.25] * (len(widths) - 2), zero, one, zero, one)
+        bl.bl_wide_mlp_apply(net, bw)
+        torch.cuda.synchronize()
+        kw = 3
+        ev[0].record(stream)
+        for _ in range(kw):
+            bl.bl_wide_mlp_apply(net, bw)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1]) / kw
+        H, L = widths[1], len(widths) - 2
+        flop = 2 * (6 * H + (L - 1) * H * H + H * 6)
+        rows.append({"hidden": [H] * L, "activation": "PReLU", "particles": npw,
+                     "ms_per_stage": ms, "ns_per_particle_stage": ms * 1e6 / npw,
+                     "particle_stages_per_s": npw / (ms * 1e-3),
+                     "tflops_algorithmic": flop * npw / (ms * 1e-3) / 1e12,
+                     "paper_A100_ns_per_particle_stage": paper_ns})
+        del net
+    try:
+        peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("bf16_tflops", 1900.0)
+    except OSError:
+        peak = 1900.0
+    for r in rows:
+        r["frac_of_bf16_peak"] = r["tflops_algorithmic"] / peak
+    return rows
+
 
 
 # ------------------------------------------------------------------- GPU arm
@@ -296,6 +346,10 @@ def main():
     if not os.path.exists(bl.LIB_PATH):
         build.build()
     bl.lib()
+    if args.paper_networks_only:
+        print(json.dumps({"paper_networks": paper_networks(bl, args.paper_particles, 2000.0, dev)}),
+              flush=True)
+        return 0
     from synth import lattice
     from synth.bunch import BunchRecipe, gaussian_bunch, training_population
 
