@@ -149,7 +149,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     W, K = args.warmup, args.steps
-    sample = max(256, args.cpu_sample // 4)
+    sample = 4096  # particles per step: about a second of host work, so K steps stay short
     for _ in range(W):
         cpu_oracle_rate(sample)
     t0 = time.perf_counter()
