@@ -146,6 +146,25 @@ int32_t bl_lattice_num_quads(const bl_lattice *lat);
 bl_status bl_track(bl_bunch *bunch, const bl_lattice *lat, double *moments_out,
                    int64_t *nonfinite_out, bl_stream stream);
 
+/* bl_track split for CUDA-graph capture: bl_track_async enqueues the same
+ * work without synchronising, allocating or touching host memory, writing
+ * the raw reductions to reduced_dev (device, or NULL for none):
+ * R * n_bunch * 28 doubles (R = bl_track_num_reductions(lat); reduction r is
+ * taken at the entry of a segment or the exit of a stage not followed by
+ * one), followed by one uint64 count of non-finite coordinates. The lattice's
+ * plan for this bunch (reference energy, dtype, bunch count) and the
+ * library's work buffers must exist before a stream capture: call bl_track or
+ * bl_track_async once on the same bunch shape first (a capture without them
+ * returns BL_ERR_INVALID_ARG). bunch->gamma_ref is advanced on the host at
+ * enqueue time; a replayed graph is valid for the captured entry energy.
+ * bl_track_expand_moments turns copied-back reductions into bl_track's
+ * moments_out (host FP64 propagation through the segments' elements). */
+int32_t bl_track_num_reductions(const bl_lattice *lat);
+bl_status bl_track_async(bl_bunch *bunch, const bl_lattice *lat, double *reduced_dev,
+                         bl_stream stream);
+bl_status bl_track_expand_moments(const bl_lattice *lat, int32_t n_bunch,
+                                  const double *reduced_host, double *moments_out);
+
 /* Per-bunch moments of the current particles (Sec. 4 moments, definitions as
  * in bl_track). out: host or device, n_bunch * 28 doubles; valid after the
  * stream is synchronised. Accumulation: exact FP32 products and float-float

@@ -85,6 +85,9 @@ _SIGS = {
     "bl_surrogate_grad": ([_P, _P, _P, _I64, _P, _I64, _P, _P, _P], C.c_int),
     "bl_surrogate_loss": ([_P, _P, _P, _I64, _P, _I64, _P, _P], C.c_int),
     "bl_track_grad": ([_P, _P, _I32, _P, _P, _P], C.c_int),
+    "bl_track_num_reductions": ([_P], C.c_int32),
+    "bl_track_async": ([_P, _P, _P, _P], C.c_int),
+    "bl_track_expand_moments": ([_P, _I32, _P, _P], C.c_int),
     "bl_wide_mlp_create": ([_P, _P], C.c_int),
     "bl_wide_mlp_destroy": ([_P], C.c_int),
     "bl_wide_mlp_apply": ([_P, _P, _I64, _P], C.c_int),
@@ -234,6 +237,62 @@ def bl_track(bunch, lattice, moments=True, stream=None):
     if st not in (BL_OK, BL_ERR_NONFINITE):
         _check(st)
     return m, (nf.value if moments else None)
+
+
+def bl_track_async(bunch, lattice, reduced=None, stream=None):
+    """Enqueue bl_track without synchronising (capturable in a CUDA graph);
+    reduced: device float64 tensor of reduced_size(lattice, bunch) or None."""
+    _check(lib().bl_track_async(bunch.ref(), lattice.handle,
+                                _ptr(reduced) if reduced is not None else None, _stream(stream)))
+
+
+def reduced_size(lattice, bunch):
+    return lib().bl_track_num_reductions(lattice.handle) * bunch.n_bunch * 28 + 1
+
+
+def bl_track_expand_moments(lattice, n_bunch, reduced_host):
+    """Moments [n_el][n_bunch][28] and the non-finite count from the raw
+    reductions copied back from bl_track_async."""
+    r = np.ascontiguousarray(reduced_host, dtype=np.float64)
+    m = np.zeros((lattice.num_elements, n_bunch, 28))
+    _check(lib().bl_track_expand_moments(lattice.handle, n_bunch, r.ctypes.data, m.ctypes.data))
+    return m, int(r[-1:].view(np.uint64)[0])
+
+
+class TrackGraph:
+    """bl_track of one bunch through one lattice captured as a CUDA graph:
+    replay() re-runs every launch of the pass (the bunch must hold new input
+    particles at the captured entry energy); moments() returns the moments of
+    the last replay."""
+
+    def __init__(self, bunch, lattice):
+        import torch
+        self.bunch, self.lattice = bunch, lattice
+        self.gamma_in = bunch.gamma_ref
+        self.reduced = torch.zeros(reduced_size(lattice, bunch), dtype=torch.float64,
+                                   device=bunch.coords[0].device)
+        # the library's work buffers belong to a stream: warm up on the
+        # stream that is then captured
+        self.stream = torch.cuda.Stream()
+        self.stream.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(self.stream):
+            bl_track_async(bunch, lattice, self.reduced)   # plan and work buffers
+        torch.cuda.synchronize()
+        bunch.struct.gamma_ref = self.gamma_in
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=self.stream):
+            bl_track_async(bunch, lattice, self.reduced)
+        self.gamma_out = bunch.gamma_ref
+
+    def replay(self):
+        self.graph.replay()
+        self.bunch.struct.gamma_ref = self.gamma_out
+
+    def moments(self):
+        import torch
+        torch.cuda.synchronize()
+        return bl_track_expand_moments(self.lattice, self.bunch.n_bunch,
+                                       self.reduced.cpu().numpy())
 
 
 def bl_moments(bunch, out=None, stream=None):

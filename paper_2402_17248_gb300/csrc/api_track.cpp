@@ -103,7 +103,7 @@ namespace {
 
 template <typename T>
 bl_status run_segment(bl_bunch *b, bl_lattice_s *L, size_t g, bool moments, double *mom_dev,
-                      cudaStream_t st) {
+                      unsigned long long *nf, cudaStream_t st) {
   auto &P = L->plan;
   Soa<T> z = soa_of<T>(b);
   const int64_t *off = b->n_bunch > 1 ? b->offsets_dev : nullptr;
@@ -114,12 +114,8 @@ bl_status run_segment(bl_bunch *b, bl_lattice_s *L, size_t g, bool moments, doub
     BL_TRY(ws_get(st, WS_PARTIALS, (size_t)stream_slots(b->n, b->n_bunch) * 28 * sizeof(double), &part));
   BL_CUDA(launch_stream<T>(z, z, b->n, off, b->n_bunch, mats, per_bunch, nullptr, true, moments,
                            (double *)part, st));
-  if (moments) {
-    void *nf = nullptr;
-    BL_TRY(ws_get(st, WS_NONFINITE, sizeof(unsigned long long), &nf));
-    BL_CUDA(launch_moments_finalize((const double *)part, off, b->n_bunch, b->n, mom_dev,
-                                    (unsigned long long *)nf, st));
-  }
+  if (moments)
+    BL_CUDA(launch_moments_finalize((const double *)part, off, b->n_bunch, b->n, mom_dev, nf, st));
   return BL_OK;
 }
 
@@ -137,6 +133,87 @@ bl_status run_stage(bl_bunch *b, bl_lattice_s *L, size_t g, cudaStream_t st) {
     BL_CUDA(launch_pusher<double>(soa_of<double>(b), b->n, tr.c, tab, st));
   }
   return BL_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// Reduction points of a lattice: segment entries, and stage exits not
+// followed by a segment. red_of[g] = index of group g's reduction or -1.
+int reduction_points(const bl_lattice_s *L, std::vector<int> *red_of) {
+  const size_t G = L->groups.size();
+  red_of->assign(G, -1);
+  int R = 0;
+  for (size_t g = 0; g < G; ++g) {
+    if (!L->groups[g].stage) (*red_of)[g] = R++;
+    else if (g + 1 == G || L->groups[g + 1].stage) (*red_of)[g] = R++;
+  }
+  return R;
+}
+
+bl_status track_checks(bl_bunch *b, bl_lattice_s *L) {
+  std::string why;
+  BL_CHECK(bunch_dims_ok(b, &why), why);
+  BL_CHECK(!lattice_has_per_bunch(L) || L->n_bunch_k == b->n_bunch,
+           "lattice per-bunch strengths do not match the bunch count");
+  for (const auto &gr : L->groups)
+    if (gr.stage && L->els[gr.first].surrogate)
+      BL_CHECK(b->dtype == BL_F32, "surrogate stages need an FP32 bunch");
+  return BL_OK;
+}
+
+// Enqueue every group; reductions (28 doubles per bunch per reduction point)
+// into mom_dev and the non-finite count into *nf when mom_dev != NULL.
+bl_status track_enqueue(bl_bunch *b, bl_lattice_s *L, double *mom_dev, unsigned long long *nf,
+                        cudaStream_t st) {
+  std::vector<int> red_of;
+  reduction_points(L, &red_of);
+  const size_t per = (size_t)b->n_bunch * 28;
+  const bool want = mom_dev != nullptr;
+  if (want) BL_CUDA(cudaMemsetAsync(nf, 0, sizeof(unsigned long long), st));
+  for (size_t g = 0; g < L->groups.size(); ++g) {
+    if (L->groups[g].stage) {
+      BL_TRY(run_stage(b, L, g, st));
+      if (want && red_of[g] >= 0) BL_TRY(moments_device(b, mom_dev + red_of[g] * per, nf, st));
+    } else if (b->dtype == BL_F32) {
+      BL_TRY(run_segment<float>(b, L, g, want, want ? mom_dev + red_of[g] * per : nullptr, nf, st));
+    } else {
+      BL_TRY(run_segment<double>(b, L, g, want, want ? mom_dev + red_of[g] * per : nullptr, nf, st));
+    }
+  }
+  b->gamma_ref = L->plan.gamma_out;
+  return BL_OK;
+}
+
+// Moments after every element from the reductions (host, FP64): a stage's
+// snapshot is the reduction at its exit (or at the next segment's entry); a
+// segment's elements are reached by propagating its entry moments through
+// the element matrices.
+void expand_moments(const bl_lattice_s *L, int n_bunch, const double *red, double *moments_out) {
+  std::vector<int> red_of;
+  reduction_points(L, &red_of);
+  const auto &P = L->plan;
+  const size_t per = (size_t)n_bunch * 28;
+  const int nbm = lattice_has_per_bunch(L) ? n_bunch : 1;
+  for (size_t g = 0; g < L->groups.size(); ++g) {
+    const auto &gr = L->groups[g];
+    if (gr.stage) {
+      const int r = red_of[g] >= 0 ? red_of[g] : red_of[g + 1];
+      std::memcpy(moments_out + (size_t)gr.first * per, red + (size_t)r * per, per * sizeof(double));
+    } else {
+      for (int bb = 0; bb < n_bunch; ++bb) {
+        double cur[28];
+        std::memcpy(cur, red + (size_t)red_of[g] * per + (size_t)bb * 28, sizeof(cur));
+        for (int e = gr.first; e <= gr.last; ++e) {
+          double nxt[28];
+          propagate_moments(P.el_mats[g][e - gr.first][nbm > 1 ? bb : 0], cur, nxt);
+          std::memcpy(moments_out + (size_t)e * per + (size_t)bb * 28, nxt, sizeof(nxt));
+          std::memcpy(cur, nxt, sizeof(cur));
+        }
+      }
+    }
+  }
 }
 
 }  // namespace
@@ -221,54 +298,30 @@ bl_status bl_segment_matrix(const bl_element *elements, int32_t n, double gamma_
 int32_t bl_lattice_num_elements(const bl_lattice *lat) { return lat ? (int32_t)lat->els.size() : -1; }
 int32_t bl_lattice_num_quads(const bl_lattice *lat) { return lat ? lat->n_quads : -1; }
 
+
 bl_status bl_track(bl_bunch *b, const bl_lattice *lat_c, double *moments_out,
                    int64_t *nonfinite_out, bl_stream stream) {
   cudaStream_t st = (cudaStream_t)stream;
-  std::string why;
   BL_CHECK(lat_c, "lattice is NULL");
-  BL_CHECK(bunch_dims_ok(b, &why), why);
   bl_lattice_s *L = const_cast<bl_lattice_s *>(lat_c);
-  BL_CHECK(!lattice_has_per_bunch(L) || L->n_bunch_k == b->n_bunch,
-           "lattice per-bunch strengths do not match the bunch count");
-  for (const auto &gr : L->groups)
-    if (gr.stage && L->els[gr.first].surrogate)
-      BL_CHECK(b->dtype == BL_F32, "surrogate stages need an FP32 bunch");
+  BL_TRY(track_checks(b, L));
   DevCtx *ctx = nullptr;
   BL_TRY(current_ctx(&ctx));
   std::lock_guard<std::mutex> lk(L->mu);
   BL_TRY(build_plan(L, b->gamma_ref, b->dtype, b->n_bunch, st));
-  const auto &P = L->plan;
   const bool want = moments_out != nullptr || nonfinite_out != nullptr;
-  const size_t G = L->groups.size();
-  // reduction points: segment entries, and stage exits not followed by a segment
-  std::vector<int> red_of(G, -1);
-  int R = 0;
-  for (size_t g = 0; g < G; ++g) {
-    if (!L->groups[g].stage) red_of[g] = R++;
-    else if (g + 1 == G || L->groups[g + 1].stage) red_of[g] = R++;
-  }
+  std::vector<int> red_of;
+  const int R = reduction_points(L, &red_of);
+  const size_t per = (size_t)b->n_bunch * 28;
   double *mom_dev = nullptr;
   void *nf = nullptr;
-  const size_t per = (size_t)b->n_bunch * 28;
   if (want) {
     void *p = nullptr;
     BL_TRY(ws_get(st, WS_MOMENTS, (size_t)R * per * sizeof(double), &p));
     mom_dev = (double *)p;
     BL_TRY(ws_get(st, WS_NONFINITE, sizeof(unsigned long long), &nf));
-    BL_CUDA(cudaMemsetAsync(nf, 0, sizeof(unsigned long long), st));
   }
-  for (size_t g = 0; g < G; ++g) {
-    if (L->groups[g].stage) {
-      BL_TRY(run_stage(b, L, g, st));
-      if (want && red_of[g] >= 0)
-        BL_TRY(moments_device(b, mom_dev + red_of[g] * per, (unsigned long long *)nf, st));
-    } else if (b->dtype == BL_F32) {
-      BL_TRY(run_segment<float>(b, L, g, want, want ? mom_dev + red_of[g] * per : nullptr, st));
-    } else {
-      BL_TRY(run_segment<double>(b, L, g, want, want ? mom_dev + red_of[g] * per : nullptr, st));
-    }
-  }
-  b->gamma_ref = P.gamma_out;
+  BL_TRY(track_enqueue(b, L, mom_dev, (unsigned long long *)nf, st));
   if (!want) return BL_OK;
   std::vector<double> red((size_t)R * per);
   unsigned long long nonfin = 0;
@@ -276,29 +329,52 @@ bl_status bl_track(bl_bunch *b, const bl_lattice *lat_c, double *moments_out,
   BL_CUDA(cudaMemcpyAsync(&nonfin, nf, sizeof(nonfin), cudaMemcpyDeviceToHost, st));
   BL_CUDA(cudaStreamSynchronize(st));
   if (nonfinite_out) *nonfinite_out = (int64_t)nonfin;
-  if (moments_out) {
-    const int nbm = lattice_has_per_bunch(L) ? b->n_bunch : 1;
-    for (size_t g = 0; g < G; ++g) {
-      const auto &gr = L->groups[g];
-      if (gr.stage) {
-        const int r = red_of[g] >= 0 ? red_of[g] : red_of[g + 1];
-        std::memcpy(moments_out + (size_t)gr.first * per, red.data() + (size_t)r * per,
-                    per * sizeof(double));
-      } else {
-        for (int bb = 0; bb < b->n_bunch; ++bb) {
-          double cur[28];
-          std::memcpy(cur, red.data() + (size_t)red_of[g] * per + (size_t)bb * 28, sizeof(cur));
-          for (int e = gr.first; e <= gr.last; ++e) {
-            double nxt[28];
-            propagate_moments(P.el_mats[g][e - gr.first][nbm > 1 ? bb : 0], cur, nxt);
-            std::memcpy(moments_out + (size_t)e * per + (size_t)bb * 28, nxt, sizeof(nxt));
-            std::memcpy(cur, nxt, sizeof(cur));
-          }
-        }
-      }
-    }
-  }
+  if (moments_out) expand_moments(L, b->n_bunch, red.data(), moments_out);
   if (nonfin) return set_error(BL_ERR_NONFINITE, std::to_string(nonfin) + " non-finite particles seen");
+  return BL_OK;
+}
+
+int32_t bl_track_num_reductions(const bl_lattice *lat) {
+  if (!lat) return -1;
+  std::vector<int> red_of;
+  return reduction_points(lat, &red_of);
+}
+
+bl_status bl_track_async(bl_bunch *b, const bl_lattice *lat_c, double *reduced_dev,
+                         bl_stream stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  BL_CHECK(lat_c, "lattice is NULL");
+  bl_lattice_s *L = const_cast<bl_lattice_s *>(lat_c);
+  BL_TRY(track_checks(b, L));
+  DevCtx *ctx = nullptr;
+  BL_TRY(current_ctx(&ctx));
+  std::lock_guard<std::mutex> lk(L->mu);
+  auto &P = L->plan;
+  int dev = -1;
+  BL_CUDA(cudaGetDevice(&dev));
+  const bool planned = P.valid && P.gamma_in == b->gamma_ref && P.dtype == b->dtype &&
+                       P.n_bunch == b->n_bunch && P.device == dev;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  BL_CUDA(cudaStreamIsCapturing(st, &cap));
+  if (cap != cudaStreamCaptureStatusNone)
+    BL_CHECK(planned, "bl_track_async under stream capture needs the lattice's plan for this "
+                      "bunch: call bl_track (or bl_track_async) once before capturing");
+  BL_TRY(build_plan(L, b->gamma_ref, b->dtype, b->n_bunch, st));
+  std::vector<int> red_of;
+  const int R = reduction_points(L, &red_of);
+  unsigned long long *nf = reduced_dev
+      ? reinterpret_cast<unsigned long long *>(reduced_dev + (size_t)R * b->n_bunch * 28)
+      : nullptr;
+  return track_enqueue(b, L, reduced_dev, nf, st);
+}
+
+bl_status bl_track_expand_moments(const bl_lattice *lat_c, int32_t n_bunch,
+                                  const double *reduced_host, double *moments_out) {
+  BL_CHECK(lat_c && reduced_host && moments_out, "NULL argument");
+  const bl_lattice_s *L = lat_c;
+  BL_CHECK(L->plan.valid && L->plan.n_bunch == n_bunch,
+           "the lattice has no plan for this bunch count: track it first");
+  expand_moments(L, n_bunch, reduced_host, moments_out);
   return BL_OK;
 }
 
