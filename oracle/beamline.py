@@ -8,9 +8,13 @@ that stage (Sec. 4.3: surrogates incorporated into the tracking loop).
 Moments are taken from the particles after every element (Sec. 4: moments
 after each stage; here after every element).
 
-Elements are dicts: {'kind': 'drift'|'quad'|'sbend', 'L', 'k', 'angle'} or
-{'kind': 'plasma', 'L', 'nsteps', 'n0_cm3', 'E0_Vpm', 'phi0',
- 'surrogate': oracle.mlp.Surrogate or None}.
+Elements are dicts: {'kind': 'drift'|'quad'|'sbend'|'plasma_lens', 'L', 'k',
+'angle'} or {'kind': 'plasma', 'L', 'nsteps', 'n0_cm3', 'E0_Vpm', 'phi0',
+'surrogate': oracle.mlp.Surrogate or None}.
+
+A surrogate with a training domain maps only the particles inside it; the
+others are pushed through the stage by the plain RK4 method, the surrogate's
+fallback (the learned map is trusted only where it was trained).
 """
 import numpy as np
 
@@ -43,7 +47,14 @@ def track(z, gamma_ref, elements, snapshots=True, bf16=False):
             if sur is None:
                 z, gamma_ref = wake.push_stage(z, gamma_ref, st)
             else:
-                z = sur.apply(z, bf16=bf16)
+                inside = sur.in_domain(z)
+                zs = sur.apply(z, bf16=bf16)
+                if not inside.all():
+                    out = ~inside
+                    zp, _ = wake.push_stage([c[out] for c in z], gamma_ref, st)
+                    for c in range(6):
+                        zs[c][out] = zp[c]
+                z = zs
                 gamma_ref = gamma_out
         else:
             bg = np.sqrt(gamma_ref * gamma_ref - 1.0)

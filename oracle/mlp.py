@@ -145,14 +145,31 @@ class Adam:
 class Surrogate:
     """A trained stage surrogate: weights plus FP64 normalisation constants."""
 
-    def __init__(self, Ws, bs, mu_in, sd_in, mu_out, sd_out, slopes=None):
+    def __init__(self, Ws, bs, mu_in, sd_in, mu_out, sd_out, slopes=None, domain=None):
         self.slopes = None if slopes is None else [float(a) for a in slopes]
+        # domain: (lo[6], hi[6]) box of the training inputs; a particle outside
+        # it is not mapped by the network (see in_domain)
+        self.domain = None if domain is None else (np.asarray(domain[0], dtype=np.float64),
+                                                   np.asarray(domain[1], dtype=np.float64))
         self.Ws = [np.asarray(W, dtype=np.float64) for W in Ws]
         self.bs = [np.asarray(b, dtype=np.float64) for b in bs]
         self.mu_in = np.asarray(mu_in, dtype=np.float64)
         self.sd_in = np.asarray(sd_in, dtype=np.float64)
         self.mu_out = np.asarray(mu_out, dtype=np.float64)
         self.sd_out = np.asarray(sd_out, dtype=np.float64)
+
+    def in_domain(self, z):
+        """Boolean mask of the particles inside the training-input box (all
+        True without a domain). Comparisons are made on the coordinates as
+        the tracked particles hold them."""
+        if self.domain is None:
+            return np.ones(len(np.asarray(z[0])), dtype=bool)
+        lo, hi = self.domain
+        m = np.ones(len(np.asarray(z[0])), dtype=bool)
+        for c in range(6):
+            v = np.asarray(z[c], dtype=np.float64)
+            m &= ~((v < lo[c]) | (v > hi[c]))
+        return m
 
     def apply(self, z, bf16=False):
         """Map relative coordinates at stage entry to those at stage exit."""
