@@ -54,10 +54,12 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--particles", type=int, default=N_PARTICLES)
-    p.add_argument("--train-steps", type=int, default=12000)
+    p.add_argument("--train-steps", type=int, default=160000)
     p.add_argument("--train-batch", type=int, default=4096)
     p.add_argument("--train-lr", type=float, default=2e-3)
     p.add_argument("--train-pairs", type=int, default=1 << 22)
+    p.add_argument("--train-t-scale", type=float, default=8.0,
+                   help="first-layer init width on the t input (1 = plain U(+-1/sqrt(fan_in)))")
     p.add_argument("--pusher-steps", type=int, default=2)
     p.add_argument("--cpu-sample", type=int, default=1 << 16)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -372,7 +374,7 @@ def main():
     surs, infos = [], []
     for s, (xin, xout, gin) in enumerate(pairs):
         sur, info = workflow.fit_surrogate(xin, xout, steps=args.train_steps, batch=args.train_batch,
-                                           lr=args.train_lr, seed=100 + s)
+                                           lr=args.train_lr, seed=100 + s, t_scale=args.train_t_scale)
         surs.append(sur)
         infos.append(info)
         log("stage %d surrogate: test loss %.3e after %d steps (%.1fs)" %
@@ -543,6 +545,7 @@ def main():
                    "particles_per_gpu": n, "stages": N_STAGES, "l2": "inputs (384 MiB) larger than L2",
                    "train": {"pairs_per_stage": nb * per, "steps": args.train_steps,
                              "batch": args.train_batch, "lr": args.train_lr,
+                             "t_init_scale": args.train_t_scale,
                              "test_loss": [i["test_loss"] for i in infos],
                              "seconds": sum(i["seconds"] for i in infos)}},
         "pusher": {"value": push_value, "unit": "particle-stages/s", "ms_per_step": push_ms,

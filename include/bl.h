@@ -278,6 +278,14 @@ bl_status bl_wide_mlp_apply(const bl_wide_mlp *m, bl_bunch *bunch, int64_t chunk
 
 bl_status bl_surrogate_create(const bl_mlp_desc *desc, bl_surrogate **out);
 bl_status bl_surrogate_destroy(bl_surrogate *s);
+/* Training-input domain of a surrogate: the box [lo_c, hi_c] (host, 6 doubles
+ * each, raw coordinates) of the inputs it was trained on; lo = hi = NULL
+ * clears it. Inside bl_track, a particle entering this surrogate's stage
+ * outside the box is not mapped by the network but pushed through the stage
+ * by the plain RK4 method (the surrogate's fallback; the learned map is
+ * trusted only where it was trained). bl_surrogate_apply and bl_track_grad
+ * map every particle with the network. */
+bl_status bl_surrogate_set_domain(bl_surrogate *s, const double *lo, const double *hi);
 
 /* Read back the FP32 master parameters (after synchronising the device):
  * W_out[l] and b_out[l] are host buffers sized like the descriptor's. */

@@ -79,6 +79,7 @@ _SIGS = {
     "bl_beam_quantities": ([_P, _D, _P], C.c_int),
     "bl_surrogate_create": ([_P, _P], C.c_int),
     "bl_surrogate_destroy": ([_P], C.c_int),
+    "bl_surrogate_set_domain": ([_P, _P, _P], C.c_int),
     "bl_surrogate_get_params": ([_P, _P, _P], C.c_int),
     "bl_surrogate_apply": ([_P, _P, _P], C.c_int),
     "bl_surrogate_train_step": ([_P, _P, _P, _I64, _P, _I64, _P, _P, _P], C.c_int),
@@ -368,11 +369,23 @@ class Surrogate:
         self.handle = C.c_void_p()
         _check(lib().bl_surrogate_create(C.byref(d), C.byref(self.handle)))
         self.mu_in, self.sd_in, self.mu_out, self.sd_out = nrm
+        self.domain = None
 
     def __del__(self):
         if getattr(self, "handle", None) and _lib is not None:
             _lib.bl_surrogate_destroy(self.handle)
             self.handle = None
+
+    def set_domain(self, lo, hi):
+        """Training-input box (raw coordinates); None clears it."""
+        if lo is None:
+            _check(lib().bl_surrogate_set_domain(self.handle, None, None))
+            self.domain = None
+            return
+        lo = np.ascontiguousarray(lo, dtype=np.float64)
+        hi = np.ascontiguousarray(hi, dtype=np.float64)
+        _check(lib().bl_surrogate_set_domain(self.handle, lo.ctypes.data, hi.ctypes.data))
+        self.domain = (lo, hi)
 
     def params(self):
         Ws = [np.zeros((WIDTHS[l + 1], WIDTHS[l]), dtype=np.float32) for l in range(5)]

@@ -119,6 +119,26 @@ bl_status bl_surrogate_create(const bl_mlp_desc *d, bl_surrogate **out) {
   return BL_OK;
 }
 
+bl_status bl_surrogate_set_domain(bl_surrogate *s, const double *lo, const double *hi) {
+  BL_TRY(check_surrogate(s));
+  if (!lo && !hi) {
+    s->has_domain = false;
+    return BL_OK;
+  }
+  BL_CHECK(lo && hi, "give both lo and hi, or neither");
+  for (int c = 0; c < 6; ++c) {
+    BL_CHECK(!std::isnan(lo[c]) && !std::isnan(hi[c]) && lo[c] <= hi[c], "domain needs lo <= hi");
+    // FP32 bounds that contain the FP64 box
+    float l = (float)lo[c], h = (float)hi[c];
+    if ((double)l > lo[c]) l = std::nextafter(l, -INFINITY);
+    if ((double)h < hi[c]) h = std::nextafter(h, INFINITY);
+    s->dom_lo[c] = l;
+    s->dom_hi[c] = h;
+  }
+  s->has_domain = true;
+  return BL_OK;
+}
+
 bl_status bl_surrogate_destroy(bl_surrogate *s) {
   free_surrogate(s);
   return BL_OK;

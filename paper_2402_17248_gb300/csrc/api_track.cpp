@@ -123,7 +123,33 @@ bl_status run_stage(bl_bunch *b, bl_lattice_s *L, size_t g, cudaStream_t st) {
   auto &P = L->plan;
   const bl_element &e = L->els[L->groups[g].first];
   const StageTrack &tr = P.stages[g];
-  if (e.surrogate) {
+  if (e.surrogate && e.surrogate->has_domain) {
+    // surrogate inside its training domain, the plain pusher outside it
+    const bl_surrogate *s = e.surrogate;
+    BL_CHECK(b->dtype == BL_F32, "surrogate stages need an FP32 bunch");
+    DevCtx *ctx = nullptr;
+    BL_TRY(current_ctx(&ctx));
+    if (!ctx->mlp_configured) {
+      BL_CUDA(mlp_forward_configure());
+      ctx->mlp_configured = true;
+    }
+    void *fb = nullptr;
+    BL_TRY(ws_get(st, WS_FALLBACK, (size_t)(b->n + 1) * sizeof(int64_t), &fb));
+    MlpDomain dom;
+    for (int c = 0; c < 6; ++c) {
+      dom.lo[c] = s->dom_lo[c];
+      dom.hi[c] = s->dom_hi[c];
+    }
+    dom.fb_count = (unsigned long long *)fb;
+    dom.fb_list = (int64_t *)fb + 1;
+    dom.fb_cap = b->n;
+    BL_CUDA(cudaMemsetAsync(dom.fb_count, 0, sizeof(unsigned long long), st));
+    BL_CUDA(launch_mlp_forward(soa_of<float>(b), b->n, s->img, s->nrm, ctx->num_sms,
+                               ctx->err_word, st, &dom));
+    const float *tab = (const float *)((const uint8_t *)P.d_tables + P.table_off[g]);
+    BL_CUDA(launch_pusher_list(soa_of<float>(b), dom.fb_list, dom.fb_count, b->n, tr.c, tab,
+                               ctx->num_sms, st));
+  } else if (e.surrogate) {
     BL_TRY(bl_surrogate_apply(e.surrogate, b, st));
   } else if (b->dtype == BL_F32) {
     const float *tab = (const float *)((const uint8_t *)P.d_tables + P.table_off[g]);

@@ -49,6 +49,10 @@ struct StageConsts {
 template <typename T>
 cudaError_t launch_pusher(Soa<T> z, int64_t n, const StageConsts &c, const T *table,
                           cudaStream_t st);
+// FP32 push of the particles list[0 .. min(*count, capacity)) only.
+cudaError_t launch_pusher_list(Soa<float> z, const int64_t *list, const unsigned long long *count,
+                               int64_t capacity, const StageConsts &c, const float *table,
+                               int num_sms, cudaStream_t st);
 
 // ---- MLP (mlp_fwd.cu, mlp_train.cu) ----
 constexpr int MLP_H = 128;
@@ -81,8 +85,17 @@ struct MlpNormF { float mu_in[6][2], inv_sd_in[6][2], mu_out[6][2], sd_out[6][2]
 cudaError_t launch_mlp_pack(const float *params, uint8_t *img, float *bias, float *wt,
                             float *wn, cudaStream_t st);
 // err: device word that receives BL_DEVERR_* flags of bounded waits.
+// Training-input box of a surrogate; particles outside it are not mapped:
+// their indices go to fb_list (fb_count counts them) for the plain pusher.
+struct MlpDomain {
+  float lo[6], hi[6];
+  int64_t *fb_list;
+  unsigned long long *fb_count;
+  int64_t fb_cap;
+};
 cudaError_t launch_mlp_forward(Soa<float> z, int64_t n, const uint8_t *img, const MlpNorm &nrm,
-                               int num_sms, unsigned *err, cudaStream_t st);
+                               int num_sms, unsigned *err, cudaStream_t st,
+                               const MlpDomain *dom = nullptr);
 cudaError_t mlp_forward_configure();
 
 // ---- wide PReLU networks (wide_mlp.cu) ----

@@ -109,7 +109,7 @@ constexpr int MAX_REGS = (16384 / (32 * WARPS_SMSP0)) / 8 * 8;
 
 __global__ void __maxnreg__(MAX_REGS)
 mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__restrict__ img,
-                   MlpNormF nrm, unsigned *err) {
+                   MlpNormF nrm, unsigned *err, MlpDomain dom) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + OFF_SLOT);
   const uint32_t sbase = tc::smem_u32(smem);
@@ -230,6 +230,13 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
     for (; ok && tile < ntiles; tile += tstride) {
       const int64_t p = tile * 128 + m;
       const bool valid = p < n;
+      // outside the training-input box: left unchanged and listed for the
+      // plain pusher (a NaN compares false and is mapped, so it stays visible)
+      bool outside = false;
+      if (dom.fb_list) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) outside |= (xin[c] < dom.lo[c]) | (xin[c] > dom.hi[c]);
+      }
       if (io) {  // normalised BF16 input row; bias hi/lo columns k = 6, 7; k = 8..15 zero
         float xn[6];
 #pragma unroll
@@ -275,7 +282,12 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
       uint32_t r[8];
       tc::tmem_ld8(t_acc, r);
       tc::tmem_ld_wait();
-      if (valid) {
+      if (valid && outside) {
+        const unsigned long long k = atomicAdd(dom.fb_count, 1ull);
+        if ((int64_t)k < dom.fb_cap) dom.fb_list[k] = p;
+        else outside = false;  // list full (cannot happen with capacity n): keep the map
+      }
+      if (valid && !outside) {
 #pragma unroll
         for (int c = 0; c < 6; ++c)
           z.c[c][p] = df_affine(__uint_as_float(r[c]), nrm.sd_out[c][0], nrm.sd_out[c][1],
@@ -468,13 +480,15 @@ cudaError_t launch_mlp_pack(const float *params, uint8_t *img, float *bias, floa
 }
 
 cudaError_t launch_mlp_forward(Soa<float> z, int64_t n, const uint8_t *img, const MlpNorm &nrm64,
-                               int num_sms, unsigned *err, cudaStream_t st) {
+                               int num_sms, unsigned *err, cudaStream_t st, const MlpDomain *dom) {
   if (n <= 0) return cudaSuccess;
   const MlpNormF nrm = mlp::norm_pairs(nrm64);
   const int64_t ntiles = (n + 127) / 128;
   int64_t grid = (ntiles + SLOTS - 1) / SLOTS;
   if (grid > num_sms) grid = num_sms;
-  mlp_forward_kernel<<<(unsigned)grid, THREADS, SMEM_BYTES, st>>>(z, n, ntiles, img, nrm, err);
+  MlpDomain d{};
+  if (dom) d = *dom;
+  mlp_forward_kernel<<<(unsigned)grid, THREADS, SMEM_BYTES, st>>>(z, n, ntiles, img, nrm, err, d);
   return cudaGetLastError();
 }
 

@@ -71,10 +71,16 @@ BL_DEV StateF axpy(const StateF &Y, float a, const StateF &k) {
           fmaf(a, k.uy, Y.uy), fmaf(a, k.dz, Y.dz), fmaf(a, k.du, Y.du)};
 }
 
+// LIST: push only the particles list[0 .. min(*count, n)) (the surrogate's
+// fallback particles); otherwise every particle p < n.
+template <bool LIST>
 __global__ void __launch_bounds__(128)
-pusher_f32(Soa<float> z, int64_t n, ConstsF c, const float4 *__restrict__ table) {
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
-       p += (int64_t)gridDim.x * blockDim.x) {
+pusher_f32(Soa<float> z, int64_t n, ConstsF c, const float4 *__restrict__ table,
+           const int64_t *__restrict__ list, const unsigned long long *count) {
+  const int64_t m = LIST ? min(n, (int64_t)*count) : n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = LIST ? list[i] : i;
     StateF Y;
     {
       const float x = z.c[0][p], px = z.c[1][p], y = z.c[2][p], py = z.c[3][p];
@@ -228,10 +234,7 @@ pusher_f64(Soa<double> z, int64_t n, StageConsts c, const D4 *__restrict__ table
 
 }  // namespace
 
-template <>
-cudaError_t launch_pusher<float>(Soa<float> z, int64_t n, const StageConsts &c,
-                                 const float *table, cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
+static ConstsF consts_f(const StageConsts &c) {
   ConstsF f;
   f.kp = (float)c.kp;
   f.g = (float)c.g;
@@ -245,8 +248,27 @@ cudaError_t launch_pusher<float>(Soa<float> z, int64_t n, const StageConsts &c,
   f.gamma_out = (float)c.gamma_out;
   f.uz_out = (float)c.uz_ref_out;
   f.nsteps = c.nsteps;
+  return f;
+}
+
+template <>
+cudaError_t launch_pusher<float>(Soa<float> z, int64_t n, const StageConsts &c,
+                                 const float *table, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
   const int64_t blocks = (n + 127) / 128;
-  pusher_f32<<<(unsigned)blocks, 128, 0, st>>>(z, n, f, reinterpret_cast<const float4 *>(table));
+  pusher_f32<false><<<(unsigned)blocks, 128, 0, st>>>(
+      z, n, consts_f(c), reinterpret_cast<const float4 *>(table), nullptr, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pusher_list(Soa<float> z, const int64_t *list, const unsigned long long *count,
+                               int64_t capacity, const StageConsts &c, const float *table,
+                               int num_sms, cudaStream_t st) {
+  if (capacity <= 0) return cudaSuccess;
+  int64_t blocks = (capacity + 127) / 128;
+  if (blocks > 4 * (int64_t)num_sms) blocks = 4 * (int64_t)num_sms;  // grid-stride over the list
+  pusher_f32<true><<<(unsigned)blocks, 128, 0, st>>>(
+      z, capacity, consts_f(c), reinterpret_cast<const float4 *>(table), list, count);
   return cudaGetLastError();
 }
 

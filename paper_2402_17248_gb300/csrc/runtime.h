@@ -54,7 +54,7 @@ bl_status current_ctx(DevCtx **out);
 // ---- workspaces ----
 enum WsSlot {
   WS_PARTIALS = 0, WS_MOMENTS, WS_NONFINITE, WS_TABLES, WS_MATS, WS_CENTERS, WS_LAMBDA,
-  WS_CKPT, WS_CROSS, WS_TRAIN, WS_LOSS, WS_WIDE0, WS_WIDE1, WS_COUNT
+  WS_CKPT, WS_CROSS, WS_TRAIN, WS_LOSS, WS_WIDE0, WS_WIDE1, WS_FALLBACK, WS_COUNT
 };
 struct Workspace {
   void *ptr[WS_COUNT] = {};
@@ -127,6 +127,8 @@ struct bl_surrogate_s {
   bl::MlpNorm nrm{};
   double mu_in[6], sd_in[6], mu_out[6], sd_out[6];
   int step = 0;
+  bool has_domain = false;      // training-input box set (bl_surrogate_set_domain)
+  float dom_lo[6], dom_hi[6];
 };
 
 struct bl_wide_mlp_s {

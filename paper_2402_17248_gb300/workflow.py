@@ -69,15 +69,30 @@ def norm_constants(x6):
 
 
 def fit_surrogate(xin, xout, steps=20000, batch=1200, lr=1e-3, lr_final=1e-5, seed=0,
-                  init_seed=None, test_frac=0.3, log_every=0, widths=bl.WIDTHS):
-    """Train one stage surrogate on device pairs; returns (surrogate, info)."""
+                  init_seed=None, test_frac=0.3, log_every=0, widths=bl.WIDTHS, t_scale=1.0,
+                  domain=True):
+    """Train one stage surrogate on device pairs; returns (surrogate, info).
+
+    t_scale > 1 draws the first layer's weights on the arrival-time input t
+    t_scale times wider and the first-layer biases U(+-t_scale/2): inside a
+    plasma stage the betatron phase advance depends strongly on a particle's
+    wake phase, i.e. on t, so the exit transverse coordinates oscillate many
+    times across the bunch in t, and hidden units spread over t resolve that
+    (with the default initialisation the transverse outputs stay at their
+    mean).
+
+    domain: record the box of the training inputs on the surrogate, so that
+    in tracking the particles outside it take the plain pusher instead."""
     from synth.bunch import mlp_init
     n = xin.shape[1]
     ntest = int(round(test_frac * n))
     ntrain = n - ntest
     mu_i, sd_i = norm_constants(xin)
     mu_o, sd_o = norm_constants(xout)
-    Ws, bs = mlp_init(list(widths), seed if init_seed is None else init_seed)
+    scale = None if t_scale == 1.0 else [1.0, 1.0, 1.0, 1.0, t_scale, 1.0]
+    Ws, bs = mlp_init(list(widths), seed if init_seed is None else init_seed,
+                      first_layer_scale=scale,
+                      first_bias_range=None if t_scale == 1.0 else 0.5 * t_scale)
     sur = bl.Surrogate(Ws, bs, mu_i, sd_i, mu_o, sd_o)
     xin = xin.contiguous()
     xout = xout.contiguous()
@@ -101,6 +116,10 @@ def fit_surrogate(xin, xout, steps=20000, batch=1200, lr=1e-3, lr_final=1e-5, se
             torch.cuda.synchronize()
             history.append((s0 + k, loss.item(), time.time() - t0))
     bl.bl_surrogate_loss(sur, test_in, test_out, loss)
+    if domain:
+        tr = xin[:, :ntrain]
+        sur.set_domain(tr.min(dim=1).values.double().cpu().numpy(),
+                       tr.max(dim=1).values.double().cpu().numpy())
     torch.cuda.synchronize()
     info = {"steps": steps, "batch": batch, "lr": lr, "lr_final": lr_final,
             "train_pairs": ntrain, "test_pairs": ntest, "test_loss": loss.item(),

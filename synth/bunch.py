@@ -127,8 +127,13 @@ def random_quad_magnitudes(n_bunches, n_quads, lo=20.0, hi=80.0, seed=0):
     return (lo + (hi - lo) * u).reshape(n_bunches, n_quads)
 
 
-def mlp_init(widths, seed):
-    """Weights W[l] (out x in) and biases b[l] ~ U(+-1/sqrt(fan_in)), float64."""
+def mlp_init(widths, seed, first_layer_scale=None, first_bias_range=None):
+    """Weights W[l] (out x in) and biases b[l] ~ U(+-1/sqrt(fan_in)), float64.
+
+    first_layer_scale: optional per-input scale factors for W[0]'s columns;
+    first_bias_range: optional r for b[0] ~ U(+-r) (its own Philox stream).
+    Together they spread the first layer's units over a wider range of an
+    input, e.g. so that a map oscillating in that input is resolvable."""
     Ws, bs = [], []
     for l in range(len(widths) - 1):
         fi, fo = widths[l], widths[l + 1]
@@ -138,4 +143,9 @@ def mlp_init(widths, seed):
         v = bound * (2.0 * u - 1.0)
         Ws.append(v[: fo * fi].reshape(fo, fi))
         bs.append(v[fo * fi:])
+    if first_layer_scale is not None:
+        Ws[0] = Ws[0] * np.asarray(first_layer_scale, dtype=np.float64)[None, :]
+    if first_bias_range is not None:
+        u, _ = uniforms(seed, np.arange(widths[1], dtype=np.uint64), 450)
+        bs[0] = first_bias_range * (2.0 * u - 1.0)
     return Ws, bs

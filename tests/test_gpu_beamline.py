@@ -194,6 +194,47 @@ def test_batched_beamline_in_a_cuda_graph():
     assert b.gamma_ref == b_eager.gamma_ref
 
 
+def test_surrogate_domain_fallback_to_pusher():
+    """A surrogate stage with a training-input box: particles inside are
+    mapped by the network, the others pushed by the plain RK4 stage (the
+    surrogate's fallback), against the oracle's hybrid stage."""
+    from paper_2402_17248_gb300 import bl
+    z, g = _bunch(20000, seed=13)
+    gpu, ora = _nets(z, 1, 95)
+    Z = np.stack(z, axis=1)
+    mu, sd = Z.mean(axis=0), Z.std(axis=0)
+    lo = (mu - 2.0 * sd).astype(np.float32).astype(np.float64)
+    hi = (mu + 2.0 * sd).astype(np.float32).astype(np.float64)
+    gpu[0].set_domain(lo, hi)
+    ora[0].domain = (lo, hi)
+    st_g = lattice.plasma(200)
+    st_g["surrogate"] = gpu[0]
+    st_o = dict(st_g, surrogate=ora[0])
+    b = to_bunch(z, g)
+    mom, nf = bl.bl_track(b, bl.Lattice([st_g]))
+    got = from_bunch(b)
+    zo, go, snaps = beamline.track(z, g, [st_o], bf16=True)
+    inside = ora[0].in_domain(z)
+    print("fallback particles: %d of %d" % ((~inside).sum(), len(inside)))
+    assert 0.1 < (~inside).mean() < 0.5
+    for a, w in zip(got, zo):
+        s_ = np.std(w)
+        # network side: the identity path of this test network carries the
+        # input through BF16 activations, so a rare rounding flip moves a
+        # particle by one BF16 ulp of its value (2^-8 relative)
+        d_in = np.abs(a[inside] - w[inside])
+        assert np.mean(d_in <= 2e-3 * s_) > 0.999
+        assert np.all(d_in <= 2e-3 * s_ + 2.0 ** -7 * np.abs(w[inside]))
+        assert np.max(np.abs(a[~inside] - w[~inside])) <= 1e-3 * s_  # FP32 vs FP64 RK4
+    # the same stage without the domain maps everything with the network
+    gpu[0].set_domain(None, None)
+    b2 = to_bunch(z, g)
+    bl.bl_track(b2, bl.Lattice([st_g]))
+    got2 = from_bunch(b2)
+    assert np.array_equal(got2[0][inside], got[0][inside])
+    assert not np.allclose(got2[0][~inside], got[0][~inside], rtol=0, atol=1e-3 * np.std(zo[0]))
+
+
 def test_batched_uneven_bunches_per_bunch_quads():
     """Bunches of uneven size stored back to back, each with its own quad
     strengths, through two surrogate stages in one bl_track call: bit-identical
