@@ -54,14 +54,14 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--particles", type=int, default=N_PARTICLES)
-    p.add_argument("--train-steps", type=int, default=160000)
-    p.add_argument("--train-batch", type=int, default=4096)
+    p.add_argument("--train-steps", type=int, default=120000)
+    p.add_argument("--train-batch", type=int, default=8192)
     p.add_argument("--train-lr", type=float, default=2e-3)
     p.add_argument("--train-pairs", type=int, default=1 << 22)
     p.add_argument("--train-t-scale", type=float, default=8.0,
                    help="first-layer init width on the t input (1 = plain U(+-1/sqrt(fan_in)))")
     p.add_argument("--pusher-steps", type=int, default=2)
-    p.add_argument("--cpu-sample", type=int, default=1 << 16)
+    p.add_argument("--cpu-sample", type=int, default=1 << 15)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the batched-bunch, adjoint and training side measurements")
