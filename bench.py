@@ -456,7 +456,9 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = t.item()
     value = world * n * N_STAGES / (ms * 1e-3)
-    launches_per_step = N_STAGES * 3  # MLP + fused segment/moments + finalize per stage
+    # per stage: MLP, fused segment map + moments, moment finalize, and the
+    # list-mode fallback pusher when the surrogate has a training domain
+    launches_per_step = sum(3 + (1 if s_.domain is not None else 0) for s_ in surs)
 
     # ---- the dominant kernel alone: tcgen05 MLP over the full bunch
     restore()
