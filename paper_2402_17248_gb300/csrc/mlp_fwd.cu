@@ -165,7 +165,7 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
       constexpr uint64_t ACT_STEP = ACT_BYTES >> 4;
       for (int64_t t0 = (int64_t)blockIdx.x * SLOTS; ok && t0 < ntiles;
            t0 += (int64_t)gridDim.x * SLOTS) {
-        const int64_t live = ntiles - t0;  // slots s < live hold a tile this round
+        const int64_t live = ntiles - t0;  // slots s < live hold a tile in this pass
 #pragma unroll
         for (int l = 0; l < 5; ++l) {
 #pragma unroll
