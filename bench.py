@@ -535,7 +535,7 @@ def main():
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     peak_src = "measured" if peaks else "fallback"
 
-    cpu = None
+    cpu = cpu_push = None
     if rank == 0 and not args.no_cpu_baseline:
         from oracle import mlp as omlp
         nets = []
@@ -548,6 +548,15 @@ def main():
         cpu = {"value": rate, "unit": "particle-stages/s", "cores": cores, "kind": "oracle",
                "sample": "FP64 numpy oracle of the trained 8-stage surrogate beamline with "
                          "moments after every element, %d particles (%.1f s)" % (args.cpu_sample, dt)}
+        # the plain method on the host: the oracle's FP64 RK4 stage push
+        from oracle import beamline as obeam, wake as owake
+        zc, gc = gaussian_bunch(BunchRecipe(n=4096, seed=0))
+        t = time.perf_counter()
+        owake.push_stage([zc[k] for k in KEYS], gc, obeam.stage_of(elements[0]))
+        dtp = time.perf_counter() - t
+        cpu_push = {"value": 4096 / dtp, "unit": "particle-stages/s", "cores": cores,
+                    "kind": "oracle", "sample": "FP64 numpy oracle RK4 push of 4096 particles "
+                    "through one 400-step stage (%.1f s)" % dtp}
 
     line = {
         "metric": METRIC, "value": value, "unit": "particle-stages/s", "n_gpus": world,
@@ -575,6 +584,7 @@ def main():
                              "frac": seg_gbs / hbm_peak, "kernel": "stream_kernel (map only)",
                              "ms_per_launch": seg_ms},
         "cpu_baseline": cpu,
+        "cpu_baseline_pusher": cpu_push,
         "e2e": {"value": e2e_value, "unit": "particle-stages/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "gpu_launches": launches_per_step * args.steps,
