@@ -286,6 +286,18 @@ bl_status bl_surrogate_destroy(bl_surrogate *s);
  * trusted only where it was trained). bl_surrogate_apply and bl_track_grad
  * map every particle with the network. */
 bl_status bl_surrogate_set_domain(bl_surrogate *s, const double *lo, const double *hi);
+/* Surrogate files, so that training can resume: the FP64 normalisation
+ * constants, the training domain, the FP32 master parameters, the Adam
+ * moments and step count (binary, with a checksum; the BF16 image is rebuilt
+ * on load). save synchronises the device; load validates the whole file
+ * (magic, version, widths, finiteness, checksum) before it allocates. */
+bl_status bl_surrogate_save(const bl_surrogate *s, const char *path);
+bl_status bl_surrogate_load(const char *path, bl_surrogate **out);
+bl_status bl_surrogate_get_norm(const bl_surrogate *s, double *mu_in, double *sd_in,
+                                double *mu_out, double *sd_out);
+/* The training domain as the kernels use it (FP32 bounds widened to contain
+ * the box given to bl_surrogate_set_domain); *has = 0 when none is set. */
+bl_status bl_surrogate_get_domain(const bl_surrogate *s, double *lo, double *hi, int32_t *has);
 
 /* Read back the FP32 master parameters (after synchronising the device):
  * W_out[l] and b_out[l] are host buffers sized like the descriptor's. */

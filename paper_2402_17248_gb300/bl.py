@@ -80,6 +80,10 @@ _SIGS = {
     "bl_surrogate_create": ([_P, _P], C.c_int),
     "bl_surrogate_destroy": ([_P], C.c_int),
     "bl_surrogate_set_domain": ([_P, _P, _P], C.c_int),
+    "bl_surrogate_save": ([_P, C.c_char_p], C.c_int),
+    "bl_surrogate_load": ([C.c_char_p, _P], C.c_int),
+    "bl_surrogate_get_norm": ([_P, _P, _P, _P, _P], C.c_int),
+    "bl_surrogate_get_domain": ([_P, _P, _P, _P], C.c_int),
     "bl_surrogate_get_params": ([_P, _P, _P], C.c_int),
     "bl_surrogate_apply": ([_P, _P, _P], C.c_int),
     "bl_surrogate_train_step": ([_P, _P, _P, _I64, _P, _I64, _P, _P, _P], C.c_int),
@@ -375,6 +379,25 @@ class Surrogate:
         if getattr(self, "handle", None) and _lib is not None:
             _lib.bl_surrogate_destroy(self.handle)
             self.handle = None
+
+    def save(self, path):
+        """Write a surrogate file (parameters, Adam state, normalisation, domain)."""
+        _check(lib().bl_surrogate_save(self.handle, os.fsencode(path)))
+
+    @classmethod
+    def load(cls, path):
+        """A surrogate from a file written by save(); training can resume."""
+        self = cls.__new__(cls)
+        self.handle = C.c_void_p()
+        _check(lib().bl_surrogate_load(os.fsencode(path), C.byref(self.handle)))
+        nrm = [np.zeros(6) for _ in range(4)]
+        _check(lib().bl_surrogate_get_norm(self.handle, *[v.ctypes.data for v in nrm]))
+        self.mu_in, self.sd_in, self.mu_out, self.sd_out = nrm
+        lo, hi, has = np.zeros(6), np.zeros(6), C.c_int32(0)
+        _check(lib().bl_surrogate_get_domain(self.handle, lo.ctypes.data, hi.ctypes.data,
+                                             C.byref(has)))
+        self.domain = (lo, hi) if has.value else None
+        return self
 
     def set_domain(self, lo, hi):
         """Training-input box (raw coordinates); None clears it."""

@@ -1,5 +1,7 @@
 // C ABI: stage surrogates (create, inference, training, loss, parameters).
 #include <cmath>
+#include <cstdio>
+#include <cstring>
 
 #include "runtime.h"
 
@@ -63,6 +65,86 @@ bl_status train_grad(bl_surrogate *s, const float *in, const float *out, int64_t
   return BL_OK;
 }
 
+// A surrogate from flat FP32 parameters, optional Adam moments (NULL: zero)
+// and step count, and FP64 normalisation constants.
+bl_status make_surrogate(const float *flat, const float *m, const float *v, int step,
+                         const double *mu_in, const double *sd_in, const double *mu_out,
+                         const double *sd_out, bl_surrogate **out) {
+  DevCtx *ctx = nullptr;
+  BL_TRY(current_ctx(&ctx));
+  auto *s = new bl_surrogate_s();
+  s->device = ctx->device;
+  auto fail = [&](cudaError_t e, const char *what) {
+    free_surrogate(s);
+    return cuda_error(e, what);
+  };
+  const size_t pb = MLP_NPARAM * sizeof(float);
+  cudaError_t e;
+  if ((e = cudaMalloc(&s->params, pb)) != cudaSuccess) return fail(e, "alloc");
+  if ((e = cudaMalloc(&s->m, pb)) != cudaSuccess) return fail(e, "alloc");
+  if ((e = cudaMalloc(&s->v, pb)) != cudaSuccess) return fail(e, "alloc");
+  if ((e = cudaMalloc(&s->img, MLP_IMG_BYTES)) != cudaSuccess) return fail(e, "alloc");
+  if ((e = cudaMalloc(&s->bias, MLP_BIAS_FLOATS * sizeof(float))) != cudaSuccess) return fail(e, "alloc");
+  if ((e = cudaMalloc(&s->wt, pb)) != cudaSuccess) return fail(e, "alloc");
+  if ((e = cudaMalloc(&s->wn, pb)) != cudaSuccess) return fail(e, "alloc");
+  if ((e = cudaMemcpy(s->params, flat, pb, cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e, "upload");
+  if (m) e = cudaMemcpy(s->m, m, pb, cudaMemcpyHostToDevice);
+  else e = cudaMemset(s->m, 0, pb);
+  if (e != cudaSuccess) return fail(e, "upload");
+  if (v) e = cudaMemcpy(s->v, v, pb, cudaMemcpyHostToDevice);
+  else e = cudaMemset(s->v, 0, pb);
+  if (e != cudaSuccess) return fail(e, "upload");
+  if ((e = launch_mlp_pack(s->params, s->img, s->bias, s->wt, s->wn, 0)) != cudaSuccess) return fail(e, "pack");
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e, "pack");
+  s->step = step;
+  for (int c = 0; c < 6; ++c) {
+    s->mu_in[c] = mu_in[c];
+    s->sd_in[c] = sd_in[c];
+    s->mu_out[c] = mu_out[c];
+    s->sd_out[c] = sd_out[c];
+    s->nrm.mu_in[c] = mu_in[c];
+    s->nrm.inv_sd_in[c] = 1.0 / sd_in[c];
+    s->nrm.mu_out[c] = mu_out[c];
+    s->nrm.sd_out[c] = sd_out[c];
+  }
+  *out = s;
+  return BL_OK;
+}
+
+// ---- surrogate files ----
+// Little-endian binary: magic "BLSURR01", int32 version (1), int32 widths[6],
+// FP64 mu_in, sd_in, mu_out, sd_out (6 each), int32 has_domain, FP32
+// dom_lo[6], dom_hi[6], int32 Adam step, FP32 params, m, v (MLP_NPARAM each),
+// then a 64-bit FNV-1a hash of every preceding byte.
+constexpr char kMagic[8] = {'B', 'L', 'S', 'U', 'R', 'R', '0', '1'};
+constexpr int32_t kVersion = 1;
+
+uint64_t fnv1a(const std::vector<uint8_t> &b, size_t n) {
+  uint64_t h = 1469598103934665603ull;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= b[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+template <typename T> void put(std::vector<uint8_t> &b, const T *v, size_t n) {
+  const uint8_t *p = reinterpret_cast<const uint8_t *>(v);
+  b.insert(b.end(), p, p + n * sizeof(T));
+}
+
+struct Reader {
+  const std::vector<uint8_t> &b;
+  size_t pos = 0;
+  template <typename T> bool get(T *v, size_t n) {
+    const size_t bytes = n * sizeof(T);
+    if (pos + bytes > b.size()) return false;
+    std::memcpy(v, b.data() + pos, bytes);
+    pos += bytes;
+    return true;
+  }
+};
+
 }  // namespace
 
 extern "C" {
@@ -71,8 +153,6 @@ bl_status bl_surrogate_create(const bl_mlp_desc *d, bl_surrogate **out) {
   BL_CHECK(out, "out is NULL");
   *out = nullptr;
   BL_TRY(check_desc(d));
-  DevCtx *ctx = nullptr;
-  BL_TRY(current_ctx(&ctx));
   std::vector<float> flat(MLP_NPARAM);
   for (int l = 0; l < 5; ++l) {
     const int fi = kWidths[l], fo = kWidths[l + 1];
@@ -85,38 +165,8 @@ bl_status bl_surrogate_create(const bl_mlp_desc *d, bl_surrogate **out) {
       flat[mlp_b_off(l) + i] = d->b[l][i];
     }
   }
-  auto *s = new bl_surrogate_s();
-  s->device = ctx->device;
-  auto fail = [&](cudaError_t e, const char *what) {
-    free_surrogate(s);
-    return cuda_error(e, what);
-  };
-  cudaError_t e;
-  if ((e = cudaMalloc(&s->params, MLP_NPARAM * sizeof(float))) != cudaSuccess) return fail(e, "alloc");
-  if ((e = cudaMalloc(&s->m, MLP_NPARAM * sizeof(float))) != cudaSuccess) return fail(e, "alloc");
-  if ((e = cudaMalloc(&s->v, MLP_NPARAM * sizeof(float))) != cudaSuccess) return fail(e, "alloc");
-  if ((e = cudaMalloc(&s->img, MLP_IMG_BYTES)) != cudaSuccess) return fail(e, "alloc");
-  if ((e = cudaMalloc(&s->bias, MLP_BIAS_FLOATS * sizeof(float))) != cudaSuccess) return fail(e, "alloc");
-  if ((e = cudaMalloc(&s->wt, MLP_NPARAM * sizeof(float))) != cudaSuccess) return fail(e, "alloc");
-  if ((e = cudaMalloc(&s->wn, MLP_NPARAM * sizeof(float))) != cudaSuccess) return fail(e, "alloc");
-  if ((e = cudaMemcpy(s->params, flat.data(), MLP_NPARAM * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
-    return fail(e, "upload");
-  if ((e = cudaMemset(s->m, 0, MLP_NPARAM * sizeof(float))) != cudaSuccess) return fail(e, "memset");
-  if ((e = cudaMemset(s->v, 0, MLP_NPARAM * sizeof(float))) != cudaSuccess) return fail(e, "memset");
-  if ((e = launch_mlp_pack(s->params, s->img, s->bias, s->wt, s->wn, 0)) != cudaSuccess) return fail(e, "pack");
-  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e, "pack");
-  for (int c = 0; c < 6; ++c) {
-    s->mu_in[c] = d->mu_in[c];
-    s->sd_in[c] = d->sd_in[c];
-    s->mu_out[c] = d->mu_out[c];
-    s->sd_out[c] = d->sd_out[c];
-    s->nrm.mu_in[c] = d->mu_in[c];
-    s->nrm.inv_sd_in[c] = 1.0 / d->sd_in[c];
-    s->nrm.mu_out[c] = d->mu_out[c];
-    s->nrm.sd_out[c] = d->sd_out[c];
-  }
-  *out = s;
-  return BL_OK;
+  return make_surrogate(flat.data(), nullptr, nullptr, 0, d->mu_in, d->sd_in, d->mu_out,
+                        d->sd_out, out);
 }
 
 bl_status bl_surrogate_set_domain(bl_surrogate *s, const double *lo, const double *hi) {
@@ -233,6 +283,116 @@ bl_status bl_surrogate_loss(const bl_surrogate *s, const float *in, const float 
   int nb2 = 0;
   BL_CUDA(launch_mlp_loss(in, out, ld, idx, count, s->wt, s->wn, s->nrm, (double *)lp, &nb2, st));
   BL_CUDA(launch_loss_finalize((const double *)lp, nb2, count, loss_out, st));
+  return BL_OK;
+}
+
+bl_status bl_surrogate_save(const bl_surrogate *s, const char *path) {
+  BL_TRY(check_surrogate(s));
+  BL_CHECK(path, "path is NULL");
+  const size_t pb = MLP_NPARAM * sizeof(float);
+  std::vector<float> P(MLP_NPARAM), M(MLP_NPARAM), V(MLP_NPARAM);
+  BL_CUDA(cudaDeviceSynchronize());
+  BL_CUDA(cudaMemcpy(P.data(), s->params, pb, cudaMemcpyDeviceToHost));
+  BL_CUDA(cudaMemcpy(M.data(), s->m, pb, cudaMemcpyDeviceToHost));
+  BL_CUDA(cudaMemcpy(V.data(), s->v, pb, cudaMemcpyDeviceToHost));
+  std::vector<uint8_t> b;
+  put(b, kMagic, 8);
+  put(b, &kVersion, 1);
+  put(b, kWidths, 6);
+  put(b, s->mu_in, 6);
+  put(b, s->sd_in, 6);
+  put(b, s->mu_out, 6);
+  put(b, s->sd_out, 6);
+  const int32_t hd = s->has_domain ? 1 : 0, step = s->step;
+  put(b, &hd, 1);
+  put(b, s->dom_lo, 6);
+  put(b, s->dom_hi, 6);
+  put(b, &step, 1);
+  put(b, P.data(), MLP_NPARAM);
+  put(b, M.data(), MLP_NPARAM);
+  put(b, V.data(), MLP_NPARAM);
+  const uint64_t h = fnv1a(b, b.size());
+  put(b, &h, 1);
+  FILE *f = std::fopen(path, "wb");
+  BL_CHECK(f, std::string("cannot open for writing: ") + path);
+  const size_t w = std::fwrite(b.data(), 1, b.size(), f);
+  const int c = std::fclose(f);
+  BL_CHECK(w == b.size() && c == 0, std::string("write failed: ") + path);
+  return BL_OK;
+}
+
+bl_status bl_surrogate_load(const char *path, bl_surrogate **out) {
+  BL_CHECK(out, "out is NULL");
+  *out = nullptr;
+  BL_CHECK(path, "path is NULL");
+  FILE *f = std::fopen(path, "rb");
+  BL_CHECK(f, std::string("cannot open: ") + path);
+  std::vector<uint8_t> b;
+  uint8_t buf[1 << 16];
+  size_t r;
+  while ((r = std::fread(buf, 1, sizeof(buf), f)) > 0) b.insert(b.end(), buf, buf + r);
+  std::fclose(f);
+  BL_CHECK(b.size() >= 8 + sizeof(uint64_t), "surrogate file too short");
+  uint64_t h = 0;
+  std::memcpy(&h, b.data() + b.size() - sizeof(uint64_t), sizeof(h));
+  BL_CHECK(h == fnv1a(b, b.size() - sizeof(uint64_t)), "surrogate file checksum mismatch");
+  Reader rd{b};
+  char magic[8];
+  int32_t ver = 0, widths[6], hd = 0, step = 0;
+  double mu_in[6], sd_in[6], mu_out[6], sd_out[6];
+  float lo[6], hi[6];
+  std::vector<float> P(MLP_NPARAM), M(MLP_NPARAM), V(MLP_NPARAM);
+  BL_CHECK(rd.get(magic, 8) && std::memcmp(magic, kMagic, 8) == 0, "not a surrogate file");
+  BL_CHECK(rd.get(&ver, 1) && ver == kVersion, "unsupported surrogate file version");
+  BL_CHECK(rd.get(widths, 6) && std::memcmp(widths, kWidths, sizeof(widths)) == 0,
+           "surrogate file widths differ from this build's 6-128-128-128-128-6");
+  const bool ok = rd.get(mu_in, 6) && rd.get(sd_in, 6) && rd.get(mu_out, 6) && rd.get(sd_out, 6) &&
+                  rd.get(&hd, 1) && rd.get(lo, 6) && rd.get(hi, 6) && rd.get(&step, 1) &&
+                  rd.get(P.data(), MLP_NPARAM) && rd.get(M.data(), MLP_NPARAM) &&
+                  rd.get(V.data(), MLP_NPARAM) && rd.pos + sizeof(uint64_t) == b.size();
+  BL_CHECK(ok, "surrogate file truncated or malformed");
+  for (int c = 0; c < 6; ++c)
+    BL_CHECK(std::isfinite(mu_in[c]) && std::isfinite(mu_out[c]) && sd_in[c] > 0.0 &&
+                 sd_out[c] > 0.0 && std::isfinite(sd_in[c]) && std::isfinite(sd_out[c]),
+             "surrogate file normalisation constants invalid");
+  for (int i = 0; i < MLP_NPARAM; ++i)
+    BL_CHECK(std::isfinite(P[i]) && std::isfinite(M[i]) && std::isfinite(V[i]),
+             "surrogate file parameters must be finite");
+  BL_CHECK(step >= 0, "surrogate file step invalid");
+  bl_surrogate *s = nullptr;
+  BL_TRY(make_surrogate(P.data(), M.data(), V.data(), step, mu_in, sd_in, mu_out, sd_out, &s));
+  if (hd) {
+    for (int c = 0; c < 6; ++c) {
+      s->dom_lo[c] = lo[c];
+      s->dom_hi[c] = hi[c];
+    }
+    s->has_domain = true;
+  }
+  *out = s;
+  return BL_OK;
+}
+
+bl_status bl_surrogate_get_domain(const bl_surrogate *s, double *lo, double *hi, int32_t *has) {
+  BL_TRY(check_surrogate(s));
+  BL_CHECK(lo && hi && has, "NULL argument");
+  *has = s->has_domain ? 1 : 0;
+  for (int c = 0; c < 6; ++c) {
+    lo[c] = s->has_domain ? s->dom_lo[c] : 0.0;
+    hi[c] = s->has_domain ? s->dom_hi[c] : 0.0;
+  }
+  return BL_OK;
+}
+
+bl_status bl_surrogate_get_norm(const bl_surrogate *s, double *mu_in, double *sd_in,
+                                double *mu_out, double *sd_out) {
+  BL_TRY(check_surrogate(s));
+  BL_CHECK(mu_in && sd_in && mu_out && sd_out, "NULL argument");
+  for (int c = 0; c < 6; ++c) {
+    mu_in[c] = s->mu_in[c];
+    sd_in[c] = s->sd_in[c];
+    mu_out[c] = s->mu_out[c];
+    sd_out[c] = s->sd_out[c];
+  }
   return BL_OK;
 }
 

@@ -94,3 +94,41 @@ def test_beam_quantities_match_oracle():
     got = bl.bl_beam_quantities(m, g)
     for k in want:
         assert abs(got[k] / want[k] - 1) < 1e-13, k
+
+
+def _surrogate_file(tmp_path, widths=(6, 128, 128, 128, 128, 6), checksum_ok=True, cut=0):
+    """Bytes in the surrogate file format (see bl_surrogate_save)."""
+    import struct
+    n = 51206
+    body = b"BLSURR01" + struct.pack("<i", 1) + struct.pack("<6i", *widths)
+    body += struct.pack("<24d", *([0.0] * 6 + [1.0] * 6 + [0.0] * 6 + [1.0] * 6))
+    body += struct.pack("<i", 0) + struct.pack("<12f", *([0.0] * 12)) + struct.pack("<i", 0)
+    body += np.zeros(3 * n, dtype=np.float32).tobytes()
+    h = 1469598103934665603
+    for byte in body:
+        h = ((h ^ byte) * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+    if not checksum_ok:
+        h ^= 1
+    data = body + struct.pack("<Q", h)
+    if cut:
+        data = data[:-cut]
+    p = tmp_path / "s.blsurr"
+    p.write_bytes(data)
+    return p
+
+
+def test_surrogate_file_validation_before_allocation(tmp_path):
+    """A surrogate file is validated on the host before any device work:
+    missing, truncated, corrupted (checksum) or foreign-shaped files are
+    rejected with BL_ERR_INVALID_ARG."""
+    with pytest.raises(bl.BlError) as e:
+        bl.Surrogate.load(tmp_path / "missing.blsurr")
+    assert e.value.status == bl.BL_ERR_INVALID_ARG
+    for kw in ({"checksum_ok": False}, {"cut": 100}, {"widths": (6, 64, 64, 64, 64, 6)}):
+        with pytest.raises(bl.BlError) as e:
+            bl.Surrogate.load(_surrogate_file(tmp_path, **kw))
+        assert e.value.status == bl.BL_ERR_INVALID_ARG, kw
+    bad = tmp_path / "bad.blsurr"
+    bad.write_bytes(b"NOTASURR" + bytes(64))
+    with pytest.raises(bl.BlError):
+        bl.Surrogate.load(bad)

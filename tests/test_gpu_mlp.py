@@ -166,3 +166,43 @@ def test_training_reduces_loss_and_adam_step():
     torch.cuda.synchronize()
     print("held-out loss %.4e -> %.4e" % (l0, loss.item()))
     assert loss.item() < 0.2 * l0
+
+
+def test_surrogate_file_round_trip_and_resume(tmp_path):
+    """save -> load gives the same parameters, normalisation, domain and
+    inference bit for bit; training resumed from the file follows the same
+    trajectory (parameters and Adam state) as training that never stopped."""
+    import torch
+    from paper_2402_17248_gb300 import bl
+    Zi, Zo = _pairs(8000, 21)
+    mu_i, sd_i = Zi.mean(axis=1), Zi.std(axis=1)
+    mu_o, sd_o = Zo.mean(axis=1), Zo.std(axis=1)
+    Ws, bs = mlp_init(WIDTHS, 9)
+    din = torch.tensor(Zi, device="cuda").contiguous()
+    dout = torch.tensor(Zo, device="cuda").contiguous()
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    idx = torch.randint(0, 8000, (60, 1024), device="cuda", generator=gen)
+    a = bl.Surrogate(Ws, bs, mu_i, sd_i, mu_o, sd_o)
+    for j in range(30):
+        bl.bl_surrogate_train_step(a, din, dout, idx=idx[j], lr=1e-3)
+    lo, hi = Zi.min(axis=1).astype(np.float64), Zi.max(axis=1).astype(np.float64)
+    a.set_domain(lo, hi)
+    torch.cuda.synchronize()
+    path = tmp_path / "stage.blsurr"
+    a.save(path)
+    b = bl.Surrogate.load(path)
+    for x, y in zip(a.params(), b.params()):
+        assert all(np.array_equal(u, v) for u, v in zip(x, y))
+    assert np.array_equal(b.mu_in, a.mu_in) and np.array_equal(b.sd_out, a.sd_out)
+    assert b.domain is not None and np.all(b.domain[0] <= lo) and np.all(b.domain[1] >= hi)
+    z, g = _bunch(3000, seed=8)
+    o1, o2 = to_bunch(z, g), to_bunch(z, g)
+    bl.bl_surrogate_apply(a, o1)
+    bl.bl_surrogate_apply(b, o2)
+    assert all(np.array_equal(u, v) for u, v in zip(from_bunch(o1), from_bunch(o2)))
+    for j in range(30, 60):  # resume: same steps on both
+        bl.bl_surrogate_train_step(a, din, dout, idx=idx[j], lr=1e-3)
+        bl.bl_surrogate_train_step(b, din, dout, idx=idx[j], lr=1e-3)
+    torch.cuda.synchronize()
+    for x, y in zip(a.params(), b.params()):
+        assert all(np.array_equal(u, v) for u, v in zip(x, y))
