@@ -1,7 +1,8 @@
 /*
- * bl_debug.h -- diagnostic entry point of libbl.so (not part of the tracking
- * API). The paper has no counterpart; it exists to check the tensor-core
- * operand layouts that the surrogate kernel relies on.
+ * bl_debug.h -- diagnostic entry points of libbl.so (not part of the tracking
+ * API). The paper has no counterpart; they check the tensor-core operand
+ * layouts that the surrogate kernel relies on and inject host-side failures
+ * for the library's error-path tests.
  */
 #ifndef BL_DEBUG_H
 #define BL_DEBUG_H
@@ -21,6 +22,11 @@ extern "C" {
  * launch error. Asynchronous on `stream` (a cudaStream_t). */
 int bl_debug_umma_probe(const void *A, const void *B, float *D, int N, int K, uint32_t ks,
                         uint32_t ns, uint32_t lbo, uint32_t sbo, void *stream);
+
+/* Host-side fault injection for failure-path tests: the next n workspace
+ * allocations of the library fail with BL_ERR_OOM before reaching the
+ * allocator (no device fault is involved). n = 0 turns it off. Returns 0. */
+int bl_debug_fail_allocations(int n);
 
 #ifdef __cplusplus
 }

@@ -99,6 +99,7 @@ _SIGS = {
     "bl_last_error_message": ([], C.c_char_p),
     "bl_version": ([], C.c_char_p),
     "bl_poll_device_errors": ([], C.c_int),
+    "bl_debug_fail_allocations": ([C.c_int], C.c_int),
     "bl_debug_umma_probe": ([_P, _P, _P, C.c_int, C.c_int, C.c_uint32, C.c_uint32,
                              C.c_uint32, C.c_uint32, _P], C.c_int),
 }
@@ -510,3 +511,8 @@ def bl_version():
 def bl_debug_umma_probe(A, B, D, N, K, ks, ns, lbo, sbo, stream=None):
     return lib().bl_debug_umma_probe(_ptr(A), _ptr(B), _ptr(D), N, K, ks, ns, lbo, sbo,
                                      _stream(stream))
+
+
+def bl_debug_fail_allocations(n):
+    return lib().bl_debug_fail_allocations(int(n))
+

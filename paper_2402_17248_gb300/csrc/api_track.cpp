@@ -1,6 +1,8 @@
 // C ABI: lattices, tracking, moments, linear maps and the plain stage push.
 #include <cmath>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "runtime.h"
 
 using namespace bl;
@@ -199,14 +201,22 @@ bl_status track_enqueue(bl_bunch *b, bl_lattice_s *L, double *mom_dev, unsigned 
   const bool want = mom_dev != nullptr;
   if (want) BL_CUDA(cudaMemsetAsync(nf, 0, sizeof(unsigned long long), st));
   for (size_t g = 0; g < L->groups.size(); ++g) {
-    if (L->groups[g].stage) {
-      BL_TRY(run_stage(b, L, g, st));
-      if (want && red_of[g] >= 0) BL_TRY(moments_device(b, mom_dev + red_of[g] * per, nf, st));
+    // one NVTX range per element group, so a profiler timeline shows the
+    // beamline's structure (no cost without a profiler attached)
+    const bool stage = L->groups[g].stage;
+    nvtxRangePushA(!stage ? "bl segment" : (L->els[L->groups[g].first].surrogate ? "bl stage: surrogate"
+                                                                               : "bl stage: pusher"));
+    bl_status r = BL_OK;
+    if (stage) {
+      r = run_stage(b, L, g, st);
+      if (r == BL_OK && want && red_of[g] >= 0) r = moments_device(b, mom_dev + red_of[g] * per, nf, st);
     } else if (b->dtype == BL_F32) {
-      BL_TRY(run_segment<float>(b, L, g, want, want ? mom_dev + red_of[g] * per : nullptr, nf, st));
+      r = run_segment<float>(b, L, g, want, want ? mom_dev + red_of[g] * per : nullptr, nf, st);
     } else {
-      BL_TRY(run_segment<double>(b, L, g, want, want ? mom_dev + red_of[g] * per : nullptr, nf, st));
+      r = run_segment<double>(b, L, g, want, want ? mom_dev + red_of[g] * per : nullptr, nf, st);
     }
+    nvtxRangePop();
+    if (r != BL_OK) return r;
   }
   b->gamma_ref = L->plan.gamma_out;
   return BL_OK;

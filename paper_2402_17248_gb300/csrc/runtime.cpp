@@ -1,5 +1,6 @@
 // Host runtime: errors, device context, workspaces, FP64 element matrices
 // and the FP64 reference-particle track of a plasma stage.
+#include <atomic>
 #include "runtime.h"
 
 #include <algorithm>
@@ -54,6 +55,9 @@ bl_status current_ctx(DevCtx **out) {
 // -------------------------------------------------------------- workspace
 static std::mutex g_ws_mu;
 static std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
+// host-side fault injection: the next N workspace allocations report an
+// out-of-memory failure without calling the allocator (bl_debug_fail_allocations)
+static std::atomic<int> g_fail_allocs{0};
 
 bl_status ws_get(cudaStream_t st, WsSlot slot, size_t bytes, void **out) {
   int dev = -1;
@@ -70,6 +74,10 @@ bl_status ws_get(cudaStream_t st, WsSlot slot, size_t bytes, void **out) {
     }
     const size_t want = bytes + bytes / 4;
     void *p = nullptr;
+    int f = g_fail_allocs.load();
+    while (f > 0 && !g_fail_allocs.compare_exchange_weak(f, f - 1)) {
+    }
+    if (f > 0) return set_error(BL_ERR_OOM, "workspace allocation: injected failure");
     cudaError_t e = cudaMalloc(&p, want);
     if (e != cudaSuccess) return cuda_error(e, "workspace allocation");
     w.ptr[slot] = p;
@@ -377,3 +385,8 @@ bl_status bl_reference_exit(const bl_element *stage, double gamma_in, double *ga
 }
 
 }  // extern "C"
+
+extern "C" int bl_debug_fail_allocations(int n) {
+  bl::g_fail_allocs.store(n < 0 ? 0 : n);
+  return 0;
+}

@@ -220,3 +220,57 @@ def test_track_plasma_lens_section(dtype):
     ptol = 1e-10 if dtype == "f64" else 1e-3  # FP32: 200-step stage, as the pusher test
     for a, w in zip(got, zo):
         assert np.max(np.abs(a - w)) <= ptol * np.std(w)
+
+
+def test_nonfinite_particles_are_counted_and_kept():
+    """NaN/inf-poisoned particles: bl_track reports them through the
+    non-finite count at every reduction point, leaves them non-finite, and
+    every other particle is tracked exactly as in a clean run."""
+    from paper_2402_17248_gb300 import bl
+    z, g = _bunch(20000, seed=14)
+    z = as_f32(z)
+    bad = [5, 1234, 19999]
+    zp = [c.copy() for c in z]
+    zp[0][bad[0]] = np.nan
+    zp[5][bad[1]] = np.inf
+    zp[4][bad[2]] = -np.inf
+    els = lattice.single_stage_transport(200)
+    L = bl.Lattice(els)
+    b = to_bunch(zp, g)
+    mom, nf = bl.bl_track(b, L)
+    R = bl.lib().bl_track_num_reductions(L.handle)
+    assert nf == len(bad) * R
+    got = from_bunch(b)
+    assert all(not np.all(np.isfinite([c[i] for c in got])) for i in bad)
+    c_ = to_bunch(z, g)
+    bl.bl_track(c_, L)
+    clean = from_bunch(c_)
+    keep = np.ones(len(z[0]), dtype=bool)
+    keep[bad] = False
+    assert all(np.array_equal(a[keep], w[keep]) for a, w in zip(got, clean))
+
+
+def test_injected_allocation_failure_is_reported_and_recovered():
+    """A workspace allocation that fails (host-side injection) surfaces as
+    BL_ERR_OOM from bl_track, and the library works normally afterwards."""
+    import torch
+    from paper_2402_17248_gb300 import bl
+    z, g = _bunch(5000, seed=15)
+    z = as_f32(z)
+    L = bl.Lattice(lattice.matching_section())
+    s = torch.cuda.Stream()  # a stream whose work buffers do not exist yet
+    with torch.cuda.stream(s):
+        b = to_bunch(z, g)
+        bl.bl_debug_fail_allocations(1)
+        with pytest.raises(bl.BlError) as e:
+            bl.bl_track(b, L, stream=s)
+        assert e.value.status == bl.BL_ERR_OOM
+        bl.bl_debug_fail_allocations(0)
+        b = to_bunch(z, g)
+        mom, nf = bl.bl_track(b, L, stream=s)
+        s.synchronize()
+    assert nf == 0
+    ref = to_bunch(z, g)
+    mref, _ = bl.bl_track(ref, L)
+    assert np.array_equal(mom, mref)
+    assert all(np.array_equal(a, w) for a, w in zip(from_bunch(b), from_bunch(ref)))
