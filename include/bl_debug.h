@@ -1,8 +1,8 @@
 /*
  * bl_debug.h -- diagnostic entry points of libbl.so (not part of the tracking
  * API). The paper has no counterpart; they check the tensor-core operand
- * layouts that the surrogate kernel relies on and inject host-side failures
- * for the library's error-path tests.
+ * layouts that the surrogate kernel relies on, inject host-side failures for
+ * the library's error-path tests and select the training kernel.
  */
 #ifndef BL_DEBUG_H
 #define BL_DEBUG_H
@@ -27,6 +27,14 @@ int bl_debug_umma_probe(const void *A, const void *B, float *D, int N, int K, ui
  * allocations of the library fail with BL_ERR_OOM before reaching the
  * allocator (no device fault is involved). n = 0 turns it off. Returns 0. */
 int bl_debug_fail_allocations(int n);
+
+/* Selects the kernel behind bl_surrogate_train_step and bl_surrogate_grad:
+ * simt = 0 (the default) the tensor-core kernel (BF16 operands, FP32
+ * accumulation, one partial row per 128-sample tile); simt != 0 the SIMT FP32
+ * kernel, kept as an independent second evaluation of the same gradient for
+ * cross-checks. Host-side switch for the whole process; call it with no
+ * training call in flight. Returns the previous setting (0 or 1). */
+int bl_debug_train_kernel(int simt);
 
 #ifdef __cplusplus
 }

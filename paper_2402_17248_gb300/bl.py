@@ -100,6 +100,7 @@ _SIGS = {
     "bl_version": ([], C.c_char_p),
     "bl_poll_device_errors": ([], C.c_int),
     "bl_debug_fail_allocations": ([C.c_int], C.c_int),
+    "bl_debug_train_kernel": ([C.c_int], C.c_int),
     "bl_debug_umma_probe": ([_P, _P, _P, C.c_int, C.c_int, C.c_uint32, C.c_uint32,
                              C.c_uint32, C.c_uint32, _P], C.c_int),
 }
@@ -515,4 +516,11 @@ def bl_debug_umma_probe(A, B, D, N, K, ks, ns, lbo, sbo, stream=None):
 
 def bl_debug_fail_allocations(n):
     return lib().bl_debug_fail_allocations(int(n))
+
+
+def bl_debug_train_kernel(simt):
+    """Select the SIMT FP32 (True) or tensor-core (False, default) gradient
+    kernel behind bl_surrogate_train_step / bl_surrogate_grad; returns the
+    previous setting."""
+    return bool(lib().bl_debug_train_kernel(1 if simt else 0))
 

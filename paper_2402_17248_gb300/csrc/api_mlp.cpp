@@ -1,4 +1,5 @@
 // C ABI: stage surrogates (create, inference, training, loss, parameters).
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -49,21 +50,47 @@ void free_surrogate(bl_surrogate_s *s) {
   delete s;
 }
 
+std::atomic<bool> g_train_simt{false};
+
+// Partial gradients and losses of one minibatch, from the tensor-core kernel
+// (default) or the SIMT FP32 kernel; *nb_out = the number of partial rows.
 bl_status train_grad(bl_surrogate *s, const float *in, const float *out, int64_t ld,
                      const int64_t *idx, int64_t batch, float **part_out, double **lp_out,
                      int *nb_out, cudaStream_t st) {
-  const int nb = mlp_grad_blocks(batch);
+  DevCtx *ctx = nullptr;
+  BL_TRY(current_ctx(&ctx));
+  const bool simt = g_train_simt.load();
+  const int nb = simt ? mlp_grad_blocks(batch) : mlp_train_tc_tiles(batch);
   void *part = nullptr, *lp = nullptr;
   BL_TRY(ws_get(st, WS_TRAIN, (size_t)nb * MLP_PSTRIDE * sizeof(float), &part));
   BL_TRY(ws_get(st, WS_LOSS, (size_t)nb * sizeof(double), &lp));
-  int nb2 = 0;
-  BL_CUDA(launch_mlp_grad(in, out, ld, idx, batch, s->wt, s->wn, s->nrm, (float *)part,
-                          (double *)lp, &nb2, st));
+  if (simt) {
+    int nb2 = 0;
+    BL_CUDA(launch_mlp_grad(in, out, ld, idx, batch, s->wt, s->wn, s->nrm, (float *)part,
+                            (double *)lp, &nb2, st));
+  } else {
+    if (!ctx->train_tc_configured) {
+      BL_CUDA(mlp_train_tc_configure());
+      ctx->train_tc_configured = true;
+    }
+    void *scratch = nullptr;
+    BL_TRY(ws_get(st, WS_TRAIN_SCRATCH, mlp_train_tc_scratch_bytes(batch), &scratch));
+    BL_CUDA(launch_mlp_grad_tc(in, out, ld, idx, batch, s->img, s->bias, s->nrm, (float *)part,
+                               (double *)lp, (uint8_t *)scratch, ctx->num_sms, ctx->err_word, st));
+  }
   *part_out = (float *)part;
   *lp_out = (double *)lp;
-  *nb_out = nb2;
+  *nb_out = nb;
   return BL_OK;
 }
+
+}  // namespace
+
+namespace bl {
+bool mlp_train_use_simt() { return g_train_simt.load(); }
+}  // namespace bl
+
+namespace {
 
 // A surrogate from flat FP32 parameters, optional Adam moments (NULL: zero)
 // and step count, and FP64 normalisation constants.
@@ -397,3 +424,7 @@ bl_status bl_surrogate_get_norm(const bl_surrogate *s, double *mu_in, double *sd
 }
 
 }  // extern "C"
+
+extern "C" int bl_debug_train_kernel(int simt) {
+  return g_train_simt.exchange(simt != 0) ? 1 : 0;
+}

@@ -129,6 +129,20 @@ cudaError_t launch_mlp_grad(const float *in, const float *out, int64_t ld, const
                             cudaStream_t st);
 // Sum partial gradients; if step > 0 apply Adam with bias correction for
 // step t = step. grad_out (device, NPARAM) and loss_out (device) optional.
+// Minibatch MSE gradient on the tensor cores (mlp_train_tc.cu): one
+// partial row per 128-sample tile (mlp_train_tc_tiles(batch) rows), from the
+// inference weight image and FP32 bias block; scratch holds the tiles' saved
+// activations (mlp_train_tc_scratch_bytes(batch) bytes).
+inline int mlp_train_tc_tiles(int64_t batch) { return (int)((batch + 127) / 128); }
+size_t mlp_train_tc_scratch_bytes(int64_t batch);
+cudaError_t mlp_train_tc_configure();
+cudaError_t launch_mlp_grad_tc(const float *in, const float *out, int64_t ld, const int64_t *idx,
+                               int64_t batch, const uint8_t *img, const float *bias,
+                               const MlpNorm &nrm, float *partials, double *loss_partials,
+                               uint8_t *scratch, int num_sms, unsigned *err, cudaStream_t st);
+// Which gradient kernel the training entry points use: false = tensor cores
+// (default), true = the SIMT FP32 kernel (bl_debug_train_kernel).
+bool mlp_train_use_simt();
 cudaError_t launch_mlp_reduce_adam(const float *partials, int nblocks, const double *loss_partials,
                                    int64_t batch, float *params, float *m, float *v, double lr,
                                    double b1, double b2, double eps, int step, float *loss_out,

@@ -47,6 +47,7 @@ struct DevCtx {
   bool mlp_configured = false;
   bool mlp_vjp_configured = false;
   bool wide_configured = false;
+  bool train_tc_configured = false;
 };
 // Context of the current device; checks the architecture (sm_103) once.
 bl_status current_ctx(DevCtx **out);
@@ -54,7 +55,7 @@ bl_status current_ctx(DevCtx **out);
 // ---- workspaces ----
 enum WsSlot {
   WS_PARTIALS = 0, WS_MOMENTS, WS_NONFINITE, WS_TABLES, WS_MATS, WS_CENTERS, WS_LAMBDA,
-  WS_CKPT, WS_CROSS, WS_TRAIN, WS_LOSS, WS_WIDE0, WS_WIDE1, WS_FALLBACK, WS_COUNT
+  WS_CKPT, WS_CROSS, WS_TRAIN, WS_LOSS, WS_WIDE0, WS_WIDE1, WS_FALLBACK, WS_TRAIN_SCRATCH, WS_COUNT
 };
 struct Workspace {
   void *ptr[WS_COUNT] = {};

@@ -97,20 +97,7 @@ def _pairs(n, seed):
     return Zi.astype(np.float32), Zo.astype(np.float32)
 
 
-def test_gradient_matches_oracle():
-    import torch
-    from paper_2402_17248_gb300 import bl
-    Zi, Zo = _pairs(1200, 11)
-    mu_i, sd_i = Zi.mean(axis=1), Zi.std(axis=1)
-    mu_o, sd_o = Zo.mean(axis=1), Zo.std(axis=1)
-    Ws, bs = mlp_init(WIDTHS, 2)
-    sur = bl.Surrogate(Ws, bs, mu_i, sd_i, mu_o, sd_o)
-    din = torch.tensor(Zi, device="cuda")
-    dout = torch.tensor(Zo, device="cuda")
-    grad = torch.zeros(bl.BL_MLP_NPARAM, device="cuda")
-    loss = torch.zeros(1, device="cuda")
-    bl.bl_surrogate_grad(sur, din, dout, grad, loss_out=loss)
-    torch.cuda.synchronize()
+def _oracle_grad(Ws, bs, Zi, Zo, mu_i, sd_i, mu_o, sd_o):
     osur = _oracle_surrogate(Ws, bs, mu_i, sd_i, mu_o, sd_o)
     X = (Zi.T.astype(np.float64) - mu_i) / sd_i
     Y = (Zo.T.astype(np.float64) - mu_o) / sd_o
@@ -120,11 +107,78 @@ def test_gradient_matches_oracle():
     flat = []
     for l in range(5):
         flat += [dW[l].ravel(), db[l].ravel()]
-    flat = np.concatenate(flat)
+    return L, np.concatenate(flat)
+
+
+@pytest.fixture(params=["tensor_core", "simt"])
+def train_kernel(request):
+    from paper_2402_17248_gb300 import bl
+    prev = bl.bl_debug_train_kernel(request.param == "simt")
+    yield request.param
+    bl.bl_debug_train_kernel(prev)
+
+
+# batch sizes: one sample, ragged tiles of the 128-sample tensor-core kernel,
+# several tiles, and more tiles than SMs (tiles looped per CTA)
+@pytest.mark.parametrize("batch", [1, 127, 129, 1200, 40000])
+def test_gradient_matches_oracle(train_kernel, batch):
+    """Minibatch MSE loss and gradient (all weights and biases, flat layout)
+    of both gradient kernels against the FP64 oracle's reverse mode with the
+    same BF16-valued weights; inputs gathered through an index vector."""
+    import torch
+    from paper_2402_17248_gb300 import bl
+    Zi, Zo = _pairs(max(1200, batch), 11)
+    mu_i, sd_i = Zi.mean(axis=1), Zi.std(axis=1)
+    mu_o, sd_o = Zo.mean(axis=1), Zo.std(axis=1)
+    Ws, bs = mlp_init(WIDTHS, 2)
+    sur = bl.Surrogate(Ws, bs, mu_i, sd_i, mu_o, sd_o)
+    din = torch.tensor(Zi, device="cuda")
+    dout = torch.tensor(Zo, device="cuda")
+    sel = np.random.default_rng(batch).permutation(Zi.shape[1])[:batch]
+    idx = torch.tensor(sel, device="cuda", dtype=torch.int64)
+    grad = torch.zeros(bl.BL_MLP_NPARAM, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    bl.bl_surrogate_grad(sur, din, dout, grad, idx=idx, loss_out=loss)
+    torch.cuda.synchronize()
+    L, flat = _oracle_grad(Ws, bs, Zi[:, sel], Zo[:, sel], mu_i, sd_i, mu_o, sd_o)
     g = grad.cpu().numpy().astype(np.float64)
     rel = np.linalg.norm(g - flat) / np.linalg.norm(flat)
-    print("loss gpu %.6e oracle %.6e; gradient normwise rel err %.3e" % (loss.item(), L, rel))
+    print("%s batch %d: loss gpu %.6e oracle %.6e; gradient normwise rel err %.3e"
+          % (train_kernel, batch, loss.item(), L, rel))
     assert abs(loss.item() / L - 1) < 1e-3
+    assert rel < 1e-2
+    # per layer: every block of the flat vector is filled, not only the large ones
+    offs = [0, 768, 896, 17280, 17408, 33792, 33920, 50304, 50432, 51200, 51206]
+    for a, b in zip(offs[:-1], offs[1:]):
+        ra = np.linalg.norm(g[a:b] - flat[a:b]) / np.linalg.norm(flat[a:b])
+        assert ra < 3e-2, (a, b, ra)
+
+
+def test_gradient_kernels_agree():
+    """The tensor-core and SIMT gradient kernels evaluate the same minibatch
+    gradient independently; they agree to the tolerance of their BF16
+    operands."""
+    import torch
+    from paper_2402_17248_gb300 import bl
+    Zi, Zo = _pairs(20000, 13)
+    mu_i, sd_i = Zi.mean(axis=1), Zi.std(axis=1)
+    mu_o, sd_o = Zo.mean(axis=1), Zo.std(axis=1)
+    Ws, bs = mlp_init(WIDTHS, 4)
+    sur = bl.Surrogate(Ws, bs, mu_i, sd_i, mu_o, sd_o)
+    din = torch.tensor(Zi, device="cuda")
+    dout = torch.tensor(Zo, device="cuda")
+    out = []
+    for simt in (False, True):
+        prev = bl.bl_debug_train_kernel(simt)
+        try:
+            g = torch.zeros(bl.BL_MLP_NPARAM, device="cuda")
+            bl.bl_surrogate_grad(sur, din, dout, g)
+            torch.cuda.synchronize()
+        finally:
+            bl.bl_debug_train_kernel(prev)
+        out.append(g.cpu().numpy().astype(np.float64))
+    rel = np.linalg.norm(out[0] - out[1]) / np.linalg.norm(out[1])
+    print("tensor-core vs SIMT gradient: normwise rel diff %.3e" % rel)
     assert rel < 1e-2
 
 
