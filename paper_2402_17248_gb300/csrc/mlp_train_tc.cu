@@ -47,8 +47,8 @@ constexpr uint32_t OFF_IMG = OFF_ACT + BUF_BYTES;
 constexpr uint32_t OFF_ONES = OFF_IMG + MLP_IMG_BYTES;
 constexpr uint32_t OFF_DSUM = OFF_ONES + 128 * 16 * 2;  // [2][4 warps][128] bias sums
 constexpr uint32_t OFF_RED = OFF_DSUM + 2 * 4 * 128 * 4;  // 128 x 6 floats + 4 doubles
-constexpr uint32_t OFF_BAR = OFF_RED + 128 * 6 * 4 + 4 * 8;  // weights, mma, epi, reload
-constexpr uint32_t OFF_SLOT = OFF_BAR + 8 * 4;
+constexpr uint32_t OFF_BAR = OFF_RED + 128 * 6 * 4 + 4 * 8;  // weights, mma, epi, reload, adj
+constexpr uint32_t OFF_SLOT = OFF_BAR + 8 * 5;
 constexpr uint32_t SMEM_BYTES = (OFF_SLOT + 4 + 127) / 128 * 128;
 static_assert(SMEM_BYTES <= 227 * 1024, "shared memory budget");
 static_assert(OFF_IMG % 1024 == 0, "weight image alignment");
@@ -187,8 +187,11 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_train_tc_kernel(TrainArgs a, u
   double *red_loss = reinterpret_cast<double *>(smem + OFF_RED + 128 * 6 * 4);
   float *dsum = reinterpret_cast<float *>(smem + OFF_DSUM);          // [2][4][128]
   const uint32_t sbase = tc::smem_u32(smem), simg = sbase + OFF_IMG;
+  // bar_mma: forward and weight-gradient MMAs done; bar_adj: adjoint MMAs
+  // (delta = W^T g) done; bar_epi: the epilogue has refilled the operands;
+  // bar_ld: an activation reload has landed
   const uint32_t bar_w = sbase + OFF_BAR, bar_mma = bar_w + 8, bar_epi = bar_w + 16,
-                 bar_ld = bar_w + 24;
+                 bar_ld = bar_w + 24, bar_adj = bar_w + 32;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (tid == 0) {
@@ -196,6 +199,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_train_tc_kernel(TrainArgs a, u
     tc::mbar_init(bar_mma, 1);
     tc::mbar_init(bar_epi, EPI_THREADS);
     tc::mbar_init(bar_ld, 1);
+    tc::mbar_init(bar_adj, 1);
     tc::fence_mbar_init();
   }
   if (warp == MMA_WARP) {
@@ -250,17 +254,22 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_train_tc_kernel(TrainArgs a, u
             tc::mma_ss(acc, d_ones, d_b1 + (uint64_t)((b - 1) * (MLP_IMG_BH >> 4)), ID_H, 1);
           } else if (b <= 7) {
             // b = 4..7, l = 4..1: dW_l^T = act_l^T g_l (N = 16 outputs for
-            // l = 4), and for l = 3, 2, 1 delta_{l-1} = W_l^T g_l
+            // l = 4), then for l = 3, 2, 1 delta_{l-1} = W_l^T g_l, each
+            // group committed to its own barrier so that the epilogue reads
+            // dW while the adjoint MMAs run
             const int l = 8 - b;
             const uint32_t id = (l == 4) ? ID_DW16 : ID_DW;
             for (int s_ = 0; s_ < 2; ++s_)
               for (int j = 0; j < 8; ++j)
                 tc::mma_ss(dw, m_act + 256 * j, m_g + s_ * G_STEP + 256 * j, id, (s_ | j) != 0);
             if (l <= 3) {
+              tc::mma_commit(bar_mma);
               const uint64_t rw = r_w1 + (uint64_t)((l - 1) * (MLP_IMG_WH >> 4));
               for (int s_ = 0; s_ < 2; ++s_)
                 for (int j = 0; j < 8; ++j)
                   tc::mma_ss(acc, d_gk + s_ * G_STEP + 16 * j, rw + 256 * j, ID_BH, (s_ | j) != 0);
+              tc::mma_commit(bar_adj);
+              continue;
             }
           } else {  // dW0 = g_0^T act0 (rows = outputs; N = 16: inputs, bias columns)
             for (int s_ = 0; s_ < 2; ++s_)
@@ -287,12 +296,10 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_train_tc_kernel(TrainArgs a, u
     // named barrier is left waiting for a thread that has gone.
     bool ok = tc::named_bar_and(1, EPI_THREADS,
                                 tc::mbar_wait(bar_w, 0, BL_DEVERR_TMA_TIMEOUT, err));
-    uint32_t ph = 0, ph_ld = 0;
+    uint32_t ph = 0, ph_ld = 0, ph_adj = 0;
     auto done = [&]() {
       tc::tmem_st_wait();
-      // shared-memory operands and the global activation scratch (read back
-      // by bulk copies) are written through the generic proxy
-      asm volatile("fence.proxy.async;" ::: "memory");
+      tc::fence_proxy_async();  // operands written through the generic proxy
       tc::fence_before();
       mbar_arrive(bar_epi);
     };
@@ -302,18 +309,25 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_train_tc_kernel(TrainArgs a, u
       ph ^= 1u;
       tc::fence_after();
     };
-    // warp 0 reloads a saved activation into the activation buffer and waits
-    // for it before the epilogue hands the buffers to the MMA warp; a failed
-    // wait reaches the other threads through the next wait_mma
-    auto reload = [&](const uint8_t *src, uint32_t bytes) {
-      if (warp == 0) {
-        if (lane == 0) {
-          tc::mbar_expect_tx(bar_ld, bytes);
-          tc::bulk_g2s(sbase + OFF_ACT, src, bytes, bar_ld);
-        }
-        __syncwarp();
-        ok = tc::mbar_wait(bar_ld, ph_ld, BL_DEVERR_TMA_TIMEOUT, err) && ok;
+    auto wait_adj = [&]() {
+      const bool got = ok && tc::mbar_wait(bar_adj, ph_adj, BL_DEVERR_MMA_TIMEOUT, err);
+      ok = tc::named_bar_and(1, EPI_THREADS, got);
+      ph_adj ^= 1u;
+      tc::fence_after();
+    };
+    // a saved activation is reloaded into the activation buffer as soon as
+    // the weight-gradient MMA that read the buffer has completed (thread 0
+    // issues the copy); warp 0 waits for it before the epilogue hands the
+    // buffers to the MMA warp, and a failed wait reaches the other threads
+    // through the next wait_mma
+    auto reload_issue = [&](const uint8_t *src, uint32_t bytes) {
+      if (tid == 0) {
+        tc::mbar_expect_tx(bar_ld, bytes);
+        tc::bulk_g2s(sbase + OFF_ACT, src, bytes, bar_ld);
       }
+    };
+    auto reload_wait = [&]() {
+      if (warp == 0) ok = tc::mbar_wait(bar_ld, ph_ld, BL_DEVERR_TMA_TIMEOUT, err) && ok;
       ph_ld ^= 1u;
     };
     // transposed weight-gradient readout of a layer l >= 1: accumulator row m
@@ -375,7 +389,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_train_tc_kernel(TrainArgs a, u
         wait_mma();
         if (!ok) break;
         uint8_t *gs = scr + 4096 + (size_t)l * 32768 + (m >> 3) * 2048 + (m & 7) * 16;
-#pragma unroll
+#pragma unroll 1
         for (int c = 0; c < 4; ++c) {
           const int f = 64 * h + 16 * c;
           uint32_t r[16];
@@ -401,7 +415,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_train_tc_kernel(TrainArgs a, u
       wait_mma();
       if (!ok) break;
       float y[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
+#pragma unroll 1
       for (int c = 0; c < 4; ++c) {
         const int f = 64 * h + 16 * c;
         uint32_t r[16];
@@ -453,13 +467,16 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_train_tc_kernel(TrainArgs a, u
 #pragma unroll
         for (int o = 0; o < 6; ++o) d4[o] = red[m * 6 + o];
       }
+      // the tile's saved activations (written above through the generic
+      // proxy) are read back by bulk copies from the next stage on
+      asm volatile("fence.proxy.async.global;" ::: "memory");
       {  // delta_4 (hi/lo) as adjoint rows: features 0..5, zeros elsewhere
         float g[16];
-#pragma unroll
+#pragma unroll 1
         for (int c = 0; c < 4; ++c) {
           const int f = 64 * h + 16 * c;
 #pragma unroll
-          for (int j = 0; j < 16; ++j) g[j] = (f + j < 6) ? d4[f + j] : 0.0f;
+          for (int j = 0; j < 16; ++j) g[j] = (f == 0 && j < 6) ? d4[j < 6 ? j : 0] : 0.0f;
           store_g16(g, gh_row, f);
           if (f == 0) warp_colsum16(g, lane, dsum + wq * 128);
         }
@@ -468,9 +485,10 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_train_tc_kernel(TrainArgs a, u
       // ---- dW4 and db4 readout; g_3 = (W4^T delta_4) * h'(z_3); act3 reloaded
       wait_mma();
       if (!ok) break;
+      reload_issue(scr + 4096 + 2 * 32768, 32768);  // act3
       dwt_out(P, 4);
       db_out(P, 4, 0, 6);
-#pragma unroll
+#pragma unroll 1
       for (int c = 0; c < 4; ++c) {
         const int f = 64 * h + 16 * c;
         uint32_t r[16];
@@ -501,18 +519,22 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_train_tc_kernel(TrainArgs a, u
         store_g16(g, gh_row, f);
         warp_colsum16(g, lane, dsum + 512 + wq * 128 + f);
       }
-      reload(scr + 4096 + 2 * 32768, 32768);  // act3
+      reload_wait();
       done();
-      // ---- layers 3, 2, 1: dW_l, db_l readout; g_{l-1} = delta_{l-1} * h';
-      // act_{l-1} reloaded
+      // ---- layers 3, 2, 1: act_{l-1} reloaded and dW_l, db_l read out while
+      // the adjoint MMA runs; then g_{l-1} = delta_{l-1} * h'
 #pragma unroll 1
       for (int l = 3; l >= 1 && ok; --l) {
-        wait_mma();
+        wait_mma();  // dW_l done: the activation buffer is free
         if (!ok) break;
+        if (l > 1) reload_issue(scr + 4096 + (size_t)(l - 2) * 32768, 32768);  // act_{l-1}
+        else reload_issue(scr, 4096);                                           // act0 (K = 16)
         dwt_out(P, l);
         db_out(P, l, l & 1, 128);   // g_3, g_1: buffer 1; g_2: buffer 0
+        wait_adj();  // delta_{l-1} done: the adjoint buffers are free
+        if (!ok) break;
         const int nb = (l - 1) & 1;  // buffer for g_{l-1}'s sums (g_0: none)
-#pragma unroll
+#pragma unroll 1
         for (int c = 0; c < 4; ++c) {
           const int f = 64 * h + 16 * c;
           uint32_t r[16], hp[8];
@@ -531,8 +553,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_train_tc_kernel(TrainArgs a, u
           store_g16(g, gh_row, f);
           if (l > 1) warp_colsum16(g, lane, dsum + nb * 512 + wq * 128 + f);
         }
-        if (l > 1) reload(scr + 4096 + (size_t)(l - 2) * 32768, 32768);  // act_{l-1}
-        else reload(scr, 4096);                                           // act0 (K = 16)
+        reload_wait();
         done();
       }
       if (!ok) break;
