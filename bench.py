@@ -195,7 +195,7 @@ def side_measurements(args, bl, workflow, lattice, surs, infos, z0, g, elements,
     secs = sum(i["seconds"] for i in infos)
     out["training"] = {"samples_per_s": steps * args.train_batch / secs, "batch": args.train_batch,
                        "steps": steps, "seconds": secs,
-                       "kernels": "mlp_grad_kernel + reduce_adam_kernel + mlp_pack_kernel per step"}
+                       "kernels": "mlp_train_tc_kernel + reduce_adam_kernel + mlp_pack_kernel per step"}
 
     # batched: 256 bunches with log-uniform counts in [1e4, 1e6] and 32 quad
     # strengths each (magnitudes U[20, 80], signs -,+,-,+), stored back to
