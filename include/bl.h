@@ -146,6 +146,31 @@ int32_t bl_lattice_num_quads(const bl_lattice *lat);
 bl_status bl_track(bl_bunch *bunch, const bl_lattice *lat, double *moments_out,
                    int64_t *nonfinite_out, bl_stream stream);
 
+/* Track one FP32 bunch that lives in HOST memory (Sec. 4.3 at scale: the
+ * beamline applied to a bunch streamed through the GPU; bunches larger than
+ * device memory work too). in_host[c] / out_host[c] (c = x, px, y, py, t,
+ * pt): n floats each in host memory; out may alias in. Page-locked buffers
+ * let the copies overlap the tracking; pageable ones work but serialise.
+ * The bunch is processed in chunks of `chunk` particles (0: 2^22): chunk i
+ * is copied in, tracked through the whole lattice and copied back, while
+ * its neighbours are being copied and tracked (two internal compute streams,
+ * one per copy direction, four device chunk buffers). Particles are tracked
+ * by the same kernels as bl_track, one by one, so out_host equals bl_track's
+ * result on a device copy of the bunch bit for bit. moments_out (host,
+ * n_elements * 28 doubles, or NULL) and nonfinite_out (host, or NULL) are
+ * bl_track's for the whole bunch: each chunk's reductions are pooled in FP64
+ * (counts add, means pool, central moments gain the parallel-axis term),
+ * equal to bl_track's up to FP64 rounding order. gamma_ref: in, the
+ * reference Lorentz factor at the entrance; out, at the exit. The lattice may
+ * carry per-bunch strengths for one bunch at most. Work already on `stream`
+ * completes first; the call returns when out_host is written (synchronous).
+ * Calls in one process run one at a time. Errors: BL_ERR_INVALID_ARG for bad
+ * arguments (checked before any work), BL_ERR_NONFINITE as bl_track,
+ * BL_ERR_CUDA / BL_ERR_OOM from the runtime (no copy is in flight on return). */
+bl_status bl_track_host(const float *const in_host[6], float *const out_host[6], int64_t n,
+                        double *gamma_ref, const bl_lattice *lat, int64_t chunk,
+                        double *moments_out, int64_t *nonfinite_out, bl_stream stream);
+
 /* bl_track split for CUDA-graph capture: bl_track_async enqueues the same
  * work without synchronising, allocating or touching host memory, writing
  * the raw reductions to reduced_dev (device, or NULL for none):

@@ -92,6 +92,7 @@ _SIGS = {
     "bl_track_grad": ([_P, _P, _I32, _P, _P, _P], C.c_int),
     "bl_track_num_reductions": ([_P], C.c_int32),
     "bl_track_async": ([_P, _P, _P, _P], C.c_int),
+    "bl_track_host": ([_P, _P, C.c_int64, _P, _P, C.c_int64, _P, _P, _P], C.c_int),
     "bl_track_expand_moments": ([_P, _I32, _P, _P], C.c_int),
     "bl_wide_mlp_create": ([_P, _P], C.c_int),
     "bl_wide_mlp_destroy": ([_P], C.c_int),
@@ -244,6 +245,40 @@ def bl_track(bunch, lattice, moments=True, stream=None):
     if st not in (BL_OK, BL_ERR_NONFINITE):
         _check(st)
     return m, (nf.value if moments else None)
+
+
+def _host_ptr(a):
+    """Address of a host float32 buffer: a CPU torch tensor or a numpy array."""
+    if hasattr(a, "data_ptr"):
+        if a.is_cuda or a.dtype.itemsize != 4 or not a.is_contiguous():
+            raise ValueError("host coordinates must be contiguous CPU float32 tensors")
+        return a.data_ptr()
+    if a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("host coordinates must be contiguous float32 arrays")
+    return a.ctypes.data
+
+
+def bl_track_host(coords_in, coords_out, gamma_ref, lattice, chunk=0, moments=True, stream=None):
+    """Track a host-resident FP32 bunch (6 arrays or CPU tensors, page-locked
+    for overlap; coords_out may be coords_in) through the lattice in chunks
+    streamed through the GPU. Returns (moments [n_el][1][28] or None,
+    nonfinite count or None, gamma_ref at the exit)."""
+    if len(coords_in) != 6 or len(coords_out) != 6:
+        raise ValueError("need 6 input and 6 output coordinate arrays")
+    n = len(coords_in[0])
+    if any(len(a) != n for a in list(coords_in) + list(coords_out)):
+        raise ValueError("coordinate arrays differ in length")
+    pin = (C.c_void_p * 6)(*[_host_ptr(a) for a in coords_in])
+    pout = (C.c_void_p * 6)(*[_host_ptr(a) for a in coords_out])
+    g = C.c_double(gamma_ref)
+    nf = C.c_int64(0)
+    m = np.zeros((lattice.num_elements, 1, 28)) if moments else None
+    st = lib().bl_track_host(pin, pout, n, C.byref(g), lattice.handle, int(chunk),
+                             m.ctypes.data if m is not None else None,
+                             C.byref(nf) if moments else None, _stream(stream))
+    if st not in (BL_OK, BL_ERR_NONFINITE):
+        _check(st)
+    return m, (nf.value if moments else None), g.value
 
 
 def bl_track_async(bunch, lattice, reduced=None, stream=None):

@@ -1,5 +1,8 @@
 // C ABI: lattices, tracking, moments, linear maps and the plain stage push.
+#include <algorithm>
 #include <cmath>
+#include <cstring>
+#include <mutex>
 
 #include <nvtx3/nvToolsExt.h>
 
@@ -252,6 +255,53 @@ void expand_moments(const bl_lattice_s *L, int n_bunch, const double *red, doubl
   }
 }
 
+// ---- host-resident bunches (bl_track_host) ----
+constexpr int HOST_BUFS = 4;  // device chunk buffers in flight
+// event slots: [0, 4) copied in, [4, 8) tracked, [8, 12) copied out (one per
+// buffer), 12 the start, 13..16 the joins of the four pipeline streams
+constexpr int EV_IN = 0, EV_TRACKED = HOST_BUFS, EV_OUT = 2 * HOST_BUFS, EV_START = 3 * HOST_BUFS,
+              EV_JOIN = EV_START + 1;
+static_assert(EV_JOIN + 4 == DevCtx::HOST_EVENTS, "bl_track_host event slots");
+constexpr int64_t HOST_CHUNK_DEFAULT = (int64_t)1 << 22;
+// one bl_track_host at a time per process: the pipeline's streams and the
+// work buffers of its compute streams are shared
+std::mutex g_host_mu;
+
+bl_status host_pipeline_init(DevCtx *ctx) {
+  if (ctx->hp_h2d) return BL_OK;
+  for (auto &s_ : ctx->hp_comp) BL_CUDA(cudaStreamCreateWithFlags(&s_, cudaStreamNonBlocking));
+  BL_CUDA(cudaStreamCreateWithFlags(&ctx->hp_d2h, cudaStreamNonBlocking));
+  for (auto &e : ctx->hp_ev) BL_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  BL_CUDA(cudaStreamCreateWithFlags(&ctx->hp_h2d, cudaStreamNonBlocking));
+  return BL_OK;
+}
+
+// Moments of a union of disjoint particle sets from the sets' own moment
+// vectors [N, 6 means, 21 central second moments with 1/N]: counts add,
+// means pool with weights N_c, and each central moment gains the
+// parallel-axis term (mu_c - mu)(mu_c - mu)^T (FP64).
+void pool_moments(const std::vector<const double *> &parts, double *out) {
+  double N = 0.0;
+  for (const double *p : parts) N += p[0];
+  std::memset(out, 0, 28 * sizeof(double));
+  out[0] = N;
+  if (!(N > 0.0)) return;
+  for (const double *p : parts)
+    if (p[0] > 0.0)
+      for (int a = 0; a < 6; ++a) out[1 + a] += p[0] * p[1 + a];
+  for (int a = 0; a < 6; ++a) out[1 + a] /= N;
+  for (const double *p : parts) {
+    if (!(p[0] > 0.0)) continue;
+    int j = 7;
+    for (int a = 0; a < 6; ++a)
+      for (int b = a; b < 6; ++b, ++j) {
+        const double da = p[1 + a] - out[1 + a], db = p[1 + b] - out[1 + b];
+        out[j] += p[0] * (p[j] + da * db);
+      }
+  }
+  for (int j = 7; j < 28; ++j) out[j] /= N;
+}
+
 }  // namespace
 
 extern "C" {
@@ -366,6 +416,127 @@ bl_status bl_track(bl_bunch *b, const bl_lattice *lat_c, double *moments_out,
   BL_CUDA(cudaStreamSynchronize(st));
   if (nonfinite_out) *nonfinite_out = (int64_t)nonfin;
   if (moments_out) expand_moments(L, b->n_bunch, red.data(), moments_out);
+  if (nonfin) return set_error(BL_ERR_NONFINITE, std::to_string(nonfin) + " non-finite particles seen");
+  return BL_OK;
+}
+
+bl_status bl_track_host(const float *const in_host[6], float *const out_host[6], int64_t n,
+                        double *gamma_ref, const bl_lattice *lat_c, int64_t chunk,
+                        double *moments_out, int64_t *nonfinite_out, bl_stream stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  BL_CHECK(lat_c, "lattice is NULL");
+  BL_CHECK(in_host && out_host && gamma_ref, "NULL argument");
+  for (int c = 0; c < 6; ++c) BL_CHECK(in_host[c] && out_host[c], "coordinate pointer is NULL");
+  BL_CHECK(n >= 1, "n must be >= 1");
+  BL_CHECK(chunk >= 0, "chunk must be >= 0");
+  BL_CHECK(*gamma_ref > 1.0 && std::isfinite(*gamma_ref), "gamma_ref must exceed 1");
+  bl_lattice_s *L = const_cast<bl_lattice_s *>(lat_c);
+  BL_CHECK(L->n_bunch_k <= 1, "bl_track_host tracks one bunch: per-bunch strengths for more "
+                              "than one bunch are not supported");
+  if (chunk == 0) chunk = HOST_CHUNK_DEFAULT;
+  if (chunk > n) chunk = n;
+  const int64_t nchunks = (n + chunk - 1) / chunk;
+  DevCtx *ctx = nullptr;
+  BL_TRY(current_ctx(&ctx));
+  std::lock_guard<std::mutex> hk(g_host_mu);
+  std::lock_guard<std::mutex> lk(L->mu);
+  BL_TRY(host_pipeline_init(ctx));
+  const double g_in = *gamma_ref;
+  BL_TRY(build_plan(L, g_in, BL_F32, 1, st));
+  const bool want = moments_out != nullptr || nonfinite_out != nullptr;
+  std::vector<int> red_of;
+  const int R = reduction_points(L, &red_of);
+  const size_t per = (size_t)R * 28 + 1;  // one chunk's reductions + its non-finite count
+  void *buf = nullptr, *red = nullptr;
+  BL_TRY(ws_get(st, WS_HOST_BUF, (size_t)HOST_BUFS * 6 * chunk * sizeof(float), &buf));
+  if (want) BL_TRY(ws_get(st, WS_HOST_RED, (size_t)nchunks * per * sizeof(double), &red));
+  float *dbuf = (float *)buf;
+  double *dred = (double *)red;
+  cudaEvent_t *ev = ctx->hp_ev;
+  cudaStream_t h2d = ctx->hp_h2d, d2h = ctx->hp_d2h;
+  cudaStream_t pipe[4] = {h2d, d2h, ctx->hp_comp[0], ctx->hp_comp[1]};
+  // the pipeline starts after the work already on the caller's stream
+  BL_CUDA(cudaEventRecord(ev[EV_START], st));
+  for (cudaStream_t s_ : pipe) BL_CUDA(cudaStreamWaitEvent(s_, ev[EV_START], 0));
+  bl_status r = BL_OK;
+  for (int64_t i = 0; i < nchunks; ++i) {
+    const int b = (int)(i % HOST_BUFS);
+    cudaStream_t cs = ctx->hp_comp[i % 2];
+    const int64_t off = i * chunk, cn = std::min(chunk, n - off);
+    float *d = dbuf + (size_t)b * 6 * chunk;
+    cudaError_t e = cudaSuccess;
+    // copy in once the chunk that last used this buffer has been copied out
+    if (i >= HOST_BUFS) e = cudaStreamWaitEvent(h2d, ev[EV_OUT + b], 0);
+    for (int c = 0; c < 6 && e == cudaSuccess; ++c)
+      e = cudaMemcpyAsync(d + (size_t)c * chunk, in_host[c] + off, cn * sizeof(float),
+                          cudaMemcpyHostToDevice, h2d);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[EV_IN + b], h2d);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[EV_IN + b], 0);
+    if (e != cudaSuccess) {
+      r = set_error(BL_ERR_CUDA, cudaGetErrorString(e));
+      break;
+    }
+    bl_bunch cb{};
+    cb.x = d;
+    cb.px = d + chunk;
+    cb.y = d + 2 * chunk;
+    cb.py = d + 3 * chunk;
+    cb.t = d + 4 * chunk;
+    cb.pt = d + 5 * chunk;
+    cb.n = cn;
+    cb.n_bunch = 1;
+    cb.dtype = BL_F32;
+    cb.gamma_ref = g_in;
+    double *mr = want ? dred + (size_t)i * per : nullptr;
+    r = track_checks(&cb, L);
+    if (r == BL_OK)
+      r = track_enqueue(&cb, L, mr,
+                        want ? reinterpret_cast<unsigned long long *>(mr + per - 1) : nullptr, cs);
+    if (r != BL_OK) break;
+    e = cudaEventRecord(ev[EV_TRACKED + b], cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(d2h, ev[EV_TRACKED + b], 0);
+    for (int c = 0; c < 6 && e == cudaSuccess; ++c)
+      e = cudaMemcpyAsync(out_host[c] + off, d + (size_t)c * chunk, cn * sizeof(float),
+                          cudaMemcpyDeviceToHost, d2h);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[EV_OUT + b], d2h);
+    if (e != cudaSuccess) {
+      r = set_error(BL_ERR_CUDA, cudaGetErrorString(e));
+      break;
+    }
+  }
+  // join: the caller's stream waits for the whole pipeline (also after an
+  // error, so that no copy into the caller's buffers is in flight on return)
+  for (int k = 0; k < 4; ++k) {
+    cudaEventRecord(ev[EV_JOIN + k], pipe[k]);
+    cudaStreamWaitEvent(st, ev[EV_JOIN + k], 0);
+  }
+  std::vector<double> hred;
+  if (r == BL_OK && want) {
+    hred.resize((size_t)nchunks * per);
+    const cudaError_t e = cudaMemcpyAsync(hred.data(), dred, hred.size() * sizeof(double),
+                                          cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) r = set_error(BL_ERR_CUDA, cudaGetErrorString(e));
+  }
+  const cudaError_t es = cudaStreamSynchronize(st);
+  if (r != BL_OK) return r;
+  if (es != cudaSuccess) return set_error(BL_ERR_CUDA, cudaGetErrorString(es));
+  *gamma_ref = L->plan.gamma_out;
+  if (!want) return BL_OK;
+  unsigned long long nonfin = 0;
+  std::vector<double> pooled((size_t)R * 28);
+  std::vector<const double *> parts((size_t)nchunks);
+  for (int rr = 0; rr < R; ++rr) {
+    for (int64_t i = 0; i < nchunks; ++i)
+      parts[i] = hred.data() + (size_t)i * per + (size_t)rr * 28;
+    pool_moments(parts, pooled.data() + (size_t)rr * 28);
+  }
+  for (int64_t i = 0; i < nchunks; ++i) {
+    unsigned long long c = 0;
+    std::memcpy(&c, hred.data() + (size_t)i * per + per - 1, sizeof(c));
+    nonfin += c;
+  }
+  if (nonfinite_out) *nonfinite_out = (int64_t)nonfin;
+  if (moments_out) expand_moments(L, 1, pooled.data(), moments_out);
   if (nonfin) return set_error(BL_ERR_NONFINITE, std::to_string(nonfin) + " non-finite particles seen");
   return BL_OK;
 }

@@ -265,9 +265,12 @@ cudaError_t launch_pusher_list(Soa<float> z, const int64_t *list, const unsigned
                                int64_t capacity, const StageConsts &c, const float *table,
                                int num_sms, cudaStream_t st) {
   if (capacity <= 0) return cudaSuccess;
-  int64_t blocks = (capacity + 127) / 128;
-  if (blocks > 4 * (int64_t)num_sms) blocks = 4 * (int64_t)num_sms;  // grid-stride over the list
-  pusher_f32<true><<<(unsigned)blocks, 128, 0, st>>>(
+  // one-warp blocks: the list is usually short, and a block this small fits
+  // beside a resident surrogate CTA (which leaves ~7.9K registers of an SM),
+  // so a fallback push can overlap another bunch chunk's network pass
+  int64_t blocks = (capacity + 31) / 32;
+  if (blocks > 16 * (int64_t)num_sms) blocks = 16 * (int64_t)num_sms;  // grid-stride over the list
+  pusher_f32<true><<<(unsigned)blocks, 32, 0, st>>>(
       z, capacity, consts_f(c), reinterpret_cast<const float4 *>(table), list, count);
   return cudaGetLastError();
 }

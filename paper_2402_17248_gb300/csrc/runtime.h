@@ -48,6 +48,14 @@ struct DevCtx {
   bool mlp_vjp_configured = false;
   bool wide_configured = false;
   bool train_tc_configured = false;
+  // bl_track_host pipeline: two compute streams, one stream per copy
+  // direction and the events that order them (created on first use)
+  cudaStream_t hp_comp[2] = {nullptr, nullptr};
+  cudaStream_t hp_h2d = nullptr, hp_d2h = nullptr;
+  // events: 4 per chunk buffer for each of copy-in, tracked, copy-out, one
+  // start and four joins (indices fixed in bl_track_host)
+  static constexpr int HOST_EVENTS = 17;
+  cudaEvent_t hp_ev[HOST_EVENTS] = {};
 };
 // Context of the current device; checks the architecture (sm_103) once.
 bl_status current_ctx(DevCtx **out);
@@ -55,7 +63,8 @@ bl_status current_ctx(DevCtx **out);
 // ---- workspaces ----
 enum WsSlot {
   WS_PARTIALS = 0, WS_MOMENTS, WS_NONFINITE, WS_TABLES, WS_MATS, WS_CENTERS, WS_LAMBDA,
-  WS_CKPT, WS_CROSS, WS_TRAIN, WS_LOSS, WS_WIDE0, WS_WIDE1, WS_FALLBACK, WS_TRAIN_SCRATCH, WS_COUNT
+  WS_CKPT, WS_CROSS, WS_TRAIN, WS_LOSS, WS_WIDE0, WS_WIDE1, WS_FALLBACK, WS_TRAIN_SCRATCH,
+  WS_HOST_BUF, WS_HOST_RED, WS_COUNT
 };
 struct Workspace {
   void *ptr[WS_COUNT] = {};

@@ -132,3 +132,27 @@ def test_surrogate_file_validation_before_allocation(tmp_path):
     bad.write_bytes(b"NOTASURR" + bytes(64))
     with pytest.raises(bl.BlError):
         bl.Surrogate.load(bad)
+
+
+def test_track_host_validation_before_any_work():
+    """bl_track_host rejects bad arguments on the host, before touching a GPU
+    (stream 0: no CUDA call is made to look one up)"""
+    L = bl.Lattice([lattice.drift(0.1), lattice.quad(0.1, 5.0)])
+    a = [np.zeros(8, dtype=np.float32) for _ in range(6)]
+    for kw in ({"gamma_ref": 1.0}, {"gamma_ref": float("nan")}, {"chunk": -1}):
+        args = {"gamma_ref": 2000.0, "chunk": 0}
+        args.update(kw)
+        with pytest.raises(bl.BlError) as e:
+            bl.bl_track_host(a, a, args["gamma_ref"], L, chunk=args["chunk"], stream=0)
+        assert e.value.status == bl.BL_ERR_INVALID_ARG
+    empty = [np.zeros(0, dtype=np.float32) for _ in range(6)]
+    with pytest.raises(bl.BlError) as e:
+        bl.bl_track_host(empty, empty, 2000.0, L, stream=0)
+    assert e.value.status == bl.BL_ERR_INVALID_ARG
+    Lb = bl.Lattice([{"kind": "quad", "L": 0.1, "k": 30.0, "per_bunch_k": [20.0, 40.0, 60.0]}],
+                    n_bunch_k=3)
+    with pytest.raises(bl.BlError) as e:
+        bl.bl_track_host(a, a, 2000.0, Lb, stream=0)
+    assert e.value.status == bl.BL_ERR_INVALID_ARG
+    with pytest.raises(ValueError):
+        bl.bl_track_host(a, [np.zeros(8, dtype=np.float64)] * 6, 2000.0, L, stream=0)
