@@ -177,6 +177,25 @@ def run_reference(args):
     return 0
 
 
+def plateau_report(infos):
+    """Per stage: steps and seconds of the fit until the held-out loss first
+    came within 10 % (and within 2x) of its final value (from the fit's loss
+    history; the seconds include the held-out evaluations)."""
+    out = []
+    for info in infos:
+        hist = info.get("history") or []
+        if not hist:
+            out.append(None)
+            continue
+        final = hist[-1][1]
+        rec = {}
+        for name, f in (("within_10pct", 1.1), ("within_2x", 2.0)):
+            st, _, sec = next((h for h in hist if h[1] <= f * final), hist[-1])
+            rec[name] = {"steps": st, "seconds": round(sec, 2)}
+        out.append(rec)
+    return out
+
+
 # ------------------------------------------------------------ side measurements
 def side_measurements(args, bl, workflow, lattice, surs, infos, z0, g, elements, dev):
     """Throughput of the other paths on the hot-path list, reported beside the
@@ -385,8 +404,11 @@ def main():
     log("training pairs ready: %d stages x %d pairs (%.1fs)" % (len(pairs), nb * per, time.time() - t_setup))
     surs, infos = [], []
     for s, (xin, xout, gin) in enumerate(pairs):
+        # held-out loss every 5000 steps (24 evaluations at the defaults), for
+        # the time to the loss plateau
         sur, info = workflow.fit_surrogate(xin, xout, steps=args.train_steps, batch=args.train_batch,
-                                           lr=args.train_lr, seed=100 + s, t_scale=args.train_t_scale)
+                                           lr=args.train_lr, seed=100 + s, t_scale=args.train_t_scale,
+                                           log_every=5)
         surs.append(sur)
         infos.append(info)
         log("stage %d surrogate: test loss %.3e after %d steps (%.1fs)" %
@@ -500,11 +522,13 @@ def main():
     push_ms = ev[0].elapsed_time(ev[1]) / args.pusher_steps
     push_value = n * N_STAGES / (push_ms * 1e-3)
 
-    # ---- end to end through the C ABI with host buffers (pinned): the
-    # bunch streamed through the GPU in 2^22-particle chunks by
-    # bl_track_host (copies in and out overlap the tracking of other chunks)
+    # ---- end to end through the C ABI with host buffers (pinned):
+    # bl_track_host copies the bunch in 2^21-particle chunks that run the
+    # first stage as they arrive, tracks the stages in between once on the
+    # device-resident bunch, and copies each chunk back as soon as it has
+    # passed the last stage and section
     out_host = [torch.empty_like(h).pin_memory() for h in host_pinned]
-    chunk = 1 << 22
+    chunk = 1 << 21
 
     def e2e_step():
         return bl.bl_track_host(host_pinned, out_host, g, lat_sur, chunk=chunk)
@@ -526,8 +550,9 @@ def main():
                     if world == 1 else None)
     nchunks = -(-n // chunk)
     n_red = bl.lib().bl_track_num_reductions(lat_sur.handle)
+    n_regions = 2 * nchunks + 1 if nchunks > 1 else 1  # head and tail per chunk, middle once
     h2d = 6 * 4 * n
-    d2h = 6 * 4 * n + nchunks * (n_red * 28 + 1) * 8
+    d2h = 6 * 4 * n + n_regions * (n_red * 28 + 1) * 8
 
     extras = {}
     if world == 1 and not args.no_extras:
@@ -577,7 +602,8 @@ def main():
                              "batch": args.train_batch, "lr": args.train_lr,
                              "t_init_scale": args.train_t_scale,
                              "test_loss": [i["test_loss"] for i in infos],
-                             "seconds": sum(i["seconds"] for i in infos)}},
+                             "seconds": sum(i["seconds"] for i in infos),
+                             "plateau": plateau_report(infos)}},
         "pusher": {"value": push_value, "unit": "particle-stages/s", "ms_per_step": push_ms,
                    "dtype": "f32", "rk4_steps_per_stage": STEPS_PER_STAGE},
         "speedup_vs_pusher": value / push_value,
@@ -594,8 +620,9 @@ def main():
         "cpu_baseline_pusher": cpu_push,
         "e2e": {"value": e2e_value, "unit": "particle-stages/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
-                "call": "bl_track_host, page-locked host buffers, %d chunks of 2^22 particles "
-                        "(copies overlapped with tracking)" % nchunks,
+                "call": "bl_track_host, page-locked host buffers, %d chunks of 2^21 particles: "
+                        "copies in overlap the first stage, copies out the last; the bunch "
+                        "stays on the device in between" % nchunks,
                 "final_second_moments_max_rel_diff_vs_device": e2e_mom_diff},
         "gpu_launches": launches_per_step * args.steps,
         **extras,

@@ -151,14 +151,20 @@ bl_status bl_track(bl_bunch *bunch, const bl_lattice *lat, double *moments_out,
  * device memory work too). in_host[c] / out_host[c] (c = x, px, y, py, t,
  * pt): n floats each in host memory; out may alias in. Page-locked buffers
  * let the copies overlap the tracking; pageable ones work but serialise.
- * The bunch is processed in chunks of `chunk` particles (0: 2^22): chunk i
- * is copied in, tracked through the whole lattice and copied back, while
- * its neighbours are being copied and tracked (two internal compute streams,
- * one per copy direction, four device chunk buffers). Particles are tracked
+ * The bunch is copied in chunks of `chunk` particles (0: 2^21 in the
+ * whole-bunch mode below, 2^22 otherwise) on internal
+ * streams (one per copy direction, two for compute). When the bunch fits in
+ * half the free device memory and the lattice has two plasma stages or more,
+ * the groups up to the first stage run chunk by chunk as the chunks arrive,
+ * the groups in between run once on the whole device-resident bunch, and
+ * the groups from the last stage on run chunk by chunk, each chunk copied
+ * back as soon as it is done. Otherwise every chunk is copied in, tracked
+ * through the whole lattice and copied back in a ring of four device chunk
+ * buffers, so bunches larger than device memory work. Particles are tracked
  * by the same kernels as bl_track, one by one, so out_host equals bl_track's
  * result on a device copy of the bunch bit for bit. moments_out (host,
  * n_elements * 28 doubles, or NULL) and nonfinite_out (host, or NULL) are
- * bl_track's for the whole bunch: each chunk's reductions are pooled in FP64
+ * bl_track's for the whole bunch: chunked reductions are pooled in FP64
  * (counts add, means pool, central moments gain the parallel-axis term),
  * equal to bl_track's up to FP64 rounding order. gamma_ref: in, the
  * reference Lorentz factor at the entrance; out, at the exit. The lattice may

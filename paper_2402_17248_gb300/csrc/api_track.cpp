@@ -194,16 +194,17 @@ bl_status track_checks(bl_bunch *b, bl_lattice_s *L) {
   return BL_OK;
 }
 
-// Enqueue every group; reductions (28 doubles per bunch per reduction point)
-// into mom_dev and the non-finite count into *nf when mom_dev != NULL.
-bl_status track_enqueue(bl_bunch *b, bl_lattice_s *L, double *mom_dev, unsigned long long *nf,
-                        cudaStream_t st) {
+// Enqueue groups [g0, g1); the reductions of those groups (28 doubles per
+// bunch per reduction point, at the point's index) go into mom_dev and their
+// non-finite count into *nf (zeroed first) when mom_dev != NULL.
+bl_status track_enqueue_range(bl_bunch *b, bl_lattice_s *L, size_t g0, size_t g1, double *mom_dev,
+                              unsigned long long *nf, cudaStream_t st) {
   std::vector<int> red_of;
   reduction_points(L, &red_of);
   const size_t per = (size_t)b->n_bunch * 28;
   const bool want = mom_dev != nullptr;
   if (want) BL_CUDA(cudaMemsetAsync(nf, 0, sizeof(unsigned long long), st));
-  for (size_t g = 0; g < L->groups.size(); ++g) {
+  for (size_t g = g0; g < g1; ++g) {
     // one NVTX range per element group, so a profiler timeline shows the
     // beamline's structure (no cost without a profiler attached)
     const bool stage = L->groups[g].stage;
@@ -221,6 +222,13 @@ bl_status track_enqueue(bl_bunch *b, bl_lattice_s *L, double *mom_dev, unsigned 
     nvtxRangePop();
     if (r != BL_OK) return r;
   }
+  return BL_OK;
+}
+
+// Every group, then the bunch's reference energy moves to the exit's.
+bl_status track_enqueue(bl_bunch *b, bl_lattice_s *L, double *mom_dev, unsigned long long *nf,
+                        cudaStream_t st) {
+  BL_TRY(track_enqueue_range(b, L, 0, L->groups.size(), mom_dev, nf, st));
   b->gamma_ref = L->plan.gamma_out;
   return BL_OK;
 }
@@ -262,7 +270,12 @@ constexpr int HOST_BUFS = 4;  // device chunk buffers in flight
 constexpr int EV_IN = 0, EV_TRACKED = HOST_BUFS, EV_OUT = 2 * HOST_BUFS, EV_START = 3 * HOST_BUFS,
               EV_JOIN = EV_START + 1;
 static_assert(EV_JOIN + 4 == DevCtx::HOST_EVENTS, "bl_track_host event slots");
-constexpr int64_t HOST_CHUNK_DEFAULT = (int64_t)1 << 22;
+// default chunk sizes: the whole-bunch mode pays the per-chunk costs (one
+// launch set, ramp and tail per kernel) only in the head and the tail, so
+// smaller chunks shorten the unoverlapped first copy in and last copy out
+// (measured on 2^24 particles: 27.0 ms per pass at 2^21, 27.4 at 2^22);
+// the chunk-through mode pays them for every group (28.2 ms at 2^22)
+constexpr int64_t HOST_CHUNK_WHOLE = (int64_t)1 << 21, HOST_CHUNK_RING = (int64_t)1 << 22;
 // one bl_track_host at a time per process: the pipeline's streams and the
 // work buffers of its compute streams are shared
 std::mutex g_host_mu;
@@ -433,9 +446,6 @@ bl_status bl_track_host(const float *const in_host[6], float *const out_host[6],
   bl_lattice_s *L = const_cast<bl_lattice_s *>(lat_c);
   BL_CHECK(L->n_bunch_k <= 1, "bl_track_host tracks one bunch: per-bunch strengths for more "
                               "than one bunch are not supported");
-  if (chunk == 0) chunk = HOST_CHUNK_DEFAULT;
-  if (chunk > n) chunk = n;
-  const int64_t nchunks = (n + chunk - 1) / chunk;
   DevCtx *ctx = nullptr;
   BL_TRY(current_ctx(&ctx));
   std::lock_guard<std::mutex> hk(g_host_mu);
@@ -446,10 +456,33 @@ bl_status bl_track_host(const float *const in_host[6], float *const out_host[6],
   const bool want = moments_out != nullptr || nonfinite_out != nullptr;
   std::vector<int> red_of;
   const int R = reduction_points(L, &red_of);
-  const size_t per = (size_t)R * 28 + 1;  // one chunk's reductions + its non-finite count
+  const size_t per = (size_t)R * 28 + 1;  // one region: R reductions + a non-finite count
+  const size_t G = L->groups.size();
+  // head: groups up to the first stage; tail: from the last stage on
+  size_t first_stage = G, last_stage = G;
+  for (size_t g = 0; g < G; ++g)
+    if (L->groups[g].stage) {
+      if (first_stage == G) first_stage = g;
+      last_stage = g;
+    }
+  // Whole-bunch mode (the bunch fits on the device and the lattice has two
+  // stages or more): only the head and the tail run chunk by chunk, so the
+  // copies in overlap the first stage and the copies out the last, and the
+  // groups in between run once on the whole bunch. Otherwise every chunk
+  // passes through the whole lattice in a four-buffer ring.
+  size_t free_b = 0, total_b = 0;
+  BL_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  const bool fits = first_stage < last_stage && (size_t)n * 6 * sizeof(float) <= free_b / 2;
+  if (chunk == 0) chunk = fits ? HOST_CHUNK_WHOLE : HOST_CHUNK_RING;
+  if (chunk > n) chunk = n;
+  const int64_t nchunks = (n + chunk - 1) / chunk;
+  const bool whole = fits && nchunks > 1;
+  const size_t h_end = first_stage + 1, t_begin = last_stage;
+  const int64_t nregions = whole ? 2 * nchunks + 1 : nchunks;
   void *buf = nullptr, *red = nullptr;
-  BL_TRY(ws_get(st, WS_HOST_BUF, (size_t)HOST_BUFS * 6 * chunk * sizeof(float), &buf));
-  if (want) BL_TRY(ws_get(st, WS_HOST_RED, (size_t)nchunks * per * sizeof(double), &red));
+  const size_t buf_floats = whole ? (size_t)6 * n : (size_t)HOST_BUFS * 6 * chunk;
+  BL_TRY(ws_get(st, WS_HOST_BUF, buf_floats * sizeof(float), &buf));
+  if (want) BL_TRY(ws_get(st, WS_HOST_RED, (size_t)nregions * per * sizeof(double), &red));
   float *dbuf = (float *)buf;
   double *dred = (double *)red;
   cudaEvent_t *ev = ctx->hp_ev;
@@ -458,52 +491,102 @@ bl_status bl_track_host(const float *const in_host[6], float *const out_host[6],
   // the pipeline starts after the work already on the caller's stream
   BL_CUDA(cudaEventRecord(ev[EV_START], st));
   for (cudaStream_t s_ : pipe) BL_CUDA(cudaStreamWaitEvent(s_, ev[EV_START], 0));
-  bl_status r = BL_OK;
-  for (int64_t i = 0; i < nchunks; ++i) {
-    const int b = (int)(i % HOST_BUFS);
-    cudaStream_t cs = ctx->hp_comp[i % 2];
-    const int64_t off = i * chunk, cn = std::min(chunk, n - off);
-    float *d = dbuf + (size_t)b * 6 * chunk;
+  // a view of particles [off, off + cn) of a device SoA whose coordinate
+  // arrays are `stride` floats apart
+  auto view = [&](float *base, size_t stride, int64_t off, int64_t cn) {
+    bl_bunch v{};
+    v.x = base + off;
+    v.px = base + stride + off;
+    v.y = base + 2 * stride + off;
+    v.py = base + 3 * stride + off;
+    v.t = base + 4 * stride + off;
+    v.pt = base + 5 * stride + off;
+    v.n = cn;
+    v.n_bunch = 1;
+    v.dtype = BL_F32;
+    v.gamma_ref = g_in;
+    return v;
+  };
+  auto region = [&](int64_t k) { return want ? dred + (size_t)k * per : nullptr; };
+  auto region_nf = [&](int64_t k) {
+    return want ? reinterpret_cast<unsigned long long *>(dred + (size_t)k * per + per - 1) : nullptr;
+  };
+  auto copies = [&](float *dst_base, size_t dst_stride, const float *const *src, int64_t off,
+                    int64_t cn, bool to_dev, cudaStream_t cs) {
     cudaError_t e = cudaSuccess;
-    // copy in once the chunk that last used this buffer has been copied out
-    if (i >= HOST_BUFS) e = cudaStreamWaitEvent(h2d, ev[EV_OUT + b], 0);
-    for (int c = 0; c < 6 && e == cudaSuccess; ++c)
-      e = cudaMemcpyAsync(d + (size_t)c * chunk, in_host[c] + off, cn * sizeof(float),
-                          cudaMemcpyHostToDevice, h2d);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[EV_IN + b], h2d);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[EV_IN + b], 0);
-    if (e != cudaSuccess) {
-      r = set_error(BL_ERR_CUDA, cudaGetErrorString(e));
-      break;
+    for (int c = 0; c < 6 && e == cudaSuccess; ++c) {
+      float *d = dst_base + (size_t)c * dst_stride + (to_dev ? off : 0);
+      e = to_dev ? cudaMemcpyAsync(d, src[c] + off, cn * sizeof(float), cudaMemcpyHostToDevice, cs)
+                 : cudaMemcpyAsync(out_host[c] + off, dst_base + (size_t)c * dst_stride + off,
+                                   cn * sizeof(float), cudaMemcpyDeviceToHost, cs);
     }
-    bl_bunch cb{};
-    cb.x = d;
-    cb.px = d + chunk;
-    cb.y = d + 2 * chunk;
-    cb.py = d + 3 * chunk;
-    cb.t = d + 4 * chunk;
-    cb.pt = d + 5 * chunk;
-    cb.n = cn;
-    cb.n_bunch = 1;
-    cb.dtype = BL_F32;
-    cb.gamma_ref = g_in;
-    double *mr = want ? dred + (size_t)i * per : nullptr;
-    r = track_checks(&cb, L);
-    if (r == BL_OK)
-      r = track_enqueue(&cb, L, mr,
-                        want ? reinterpret_cast<unsigned long long *>(mr + per - 1) : nullptr, cs);
-    if (r != BL_OK) break;
-    e = cudaEventRecord(ev[EV_TRACKED + b], cs);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(d2h, ev[EV_TRACKED + b], 0);
-    for (int c = 0; c < 6 && e == cudaSuccess; ++c)
-      e = cudaMemcpyAsync(out_host[c] + off, d + (size_t)c * chunk, cn * sizeof(float),
-                          cudaMemcpyDeviceToHost, d2h);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[EV_OUT + b], d2h);
-    if (e != cudaSuccess) {
-      r = set_error(BL_ERR_CUDA, cudaGetErrorString(e));
-      break;
+    return e;
+  };
+  // record `e_` on `from`, make `to` wait for it (the event can be reused at once)
+  auto link = [&](cudaStream_t from, cudaStream_t to, cudaEvent_t e_) {
+    cudaError_t e = cudaEventRecord(e_, from);
+    return e == cudaSuccess ? cudaStreamWaitEvent(to, e_, 0) : e;
+  };
+  bl_status r = BL_OK;
+  cudaError_t e = cudaSuccess;
+  if (whole) {
+    // head, chunk by chunk on alternating compute streams, each chunk as soon
+    // as it has arrived
+    for (int64_t i = 0; i < nchunks && r == BL_OK && e == cudaSuccess; ++i) {
+      cudaStream_t cs = ctx->hp_comp[i % 2];
+      const int64_t off = i * chunk, cn = std::min(chunk, n - off);
+      e = copies(dbuf, n, in_host, off, cn, true, h2d);
+      if (e == cudaSuccess) e = link(h2d, cs, ev[EV_IN]);
+      if (e != cudaSuccess) break;
+      bl_bunch v = view(dbuf, n, off, cn);
+      r = track_checks(&v, L);
+      if (r == BL_OK) r = track_enqueue_range(&v, L, 0, h_end, region(i), region_nf(i), cs);
+    }
+    // the groups in between, once, on the whole bunch
+    if (r == BL_OK && e == cudaSuccess) e = link(ctx->hp_comp[1], ctx->hp_comp[0], ev[EV_IN + 1]);
+    if (r == BL_OK && e == cudaSuccess) {
+      bl_bunch v = view(dbuf, n, 0, n);
+      r = track_enqueue_range(&v, L, h_end, t_begin, region(nchunks), region_nf(nchunks),
+                              ctx->hp_comp[0]);
+    }
+    if (r == BL_OK && e == cudaSuccess) e = link(ctx->hp_comp[0], ctx->hp_comp[1], ev[EV_IN + 2]);
+    // tail, chunk by chunk, each chunk copied out as soon as it is done
+    for (int64_t i = 0; i < nchunks && r == BL_OK && e == cudaSuccess; ++i) {
+      cudaStream_t cs = ctx->hp_comp[i % 2];
+      const int64_t off = i * chunk, cn = std::min(chunk, n - off);
+      bl_bunch v = view(dbuf, n, off, cn);
+      r = track_enqueue_range(&v, L, t_begin, G, region(nchunks + 1 + i),
+                              region_nf(nchunks + 1 + i), cs);
+      if (r == BL_OK) e = link(cs, d2h, ev[EV_TRACKED]);
+      if (r == BL_OK && e == cudaSuccess) e = copies(dbuf, n, nullptr, off, cn, false, d2h);
+    }
+  } else {
+    for (int64_t i = 0; i < nchunks && r == BL_OK && e == cudaSuccess; ++i) {
+      const int b = (int)(i % HOST_BUFS);
+      cudaStream_t cs = ctx->hp_comp[i % 2];
+      const int64_t off = i * chunk, cn = std::min(chunk, n - off);
+      float *d = dbuf + (size_t)b * 6 * chunk;
+      // copy in once the chunk that last used this buffer has been copied out
+      if (i >= HOST_BUFS) e = cudaStreamWaitEvent(h2d, ev[EV_OUT + b], 0);
+      // the chunk buffer holds coordinate arrays `chunk` floats apart; the
+      // copies address it as a view at offset 0
+      for (int c = 0; c < 6 && e == cudaSuccess; ++c)
+        e = cudaMemcpyAsync(d + (size_t)c * chunk, in_host[c] + off, cn * sizeof(float),
+                            cudaMemcpyHostToDevice, h2d);
+      if (e == cudaSuccess) e = link(h2d, cs, ev[EV_IN + b]);
+      if (e != cudaSuccess) break;
+      bl_bunch v = view(d, chunk, 0, cn);
+      r = track_checks(&v, L);
+      if (r == BL_OK) r = track_enqueue_range(&v, L, 0, G, region(i), region_nf(i), cs);
+      if (r != BL_OK) break;
+      e = link(cs, d2h, ev[EV_TRACKED + b]);
+      for (int c = 0; c < 6 && e == cudaSuccess; ++c)
+        e = cudaMemcpyAsync(out_host[c] + off, d + (size_t)c * chunk, cn * sizeof(float),
+                            cudaMemcpyDeviceToHost, d2h);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[EV_OUT + b], d2h);
     }
   }
+  if (r == BL_OK && e != cudaSuccess) r = set_error(BL_ERR_CUDA, cudaGetErrorString(e));
   // join: the caller's stream waits for the whole pipeline (also after an
   // error, so that no copy into the caller's buffers is in flight on return)
   for (int k = 0; k < 4; ++k) {
@@ -512,27 +595,43 @@ bl_status bl_track_host(const float *const in_host[6], float *const out_host[6],
   }
   std::vector<double> hred;
   if (r == BL_OK && want) {
-    hred.resize((size_t)nchunks * per);
-    const cudaError_t e = cudaMemcpyAsync(hred.data(), dred, hred.size() * sizeof(double),
-                                          cudaMemcpyDeviceToHost, st);
-    if (e != cudaSuccess) r = set_error(BL_ERR_CUDA, cudaGetErrorString(e));
+    hred.resize((size_t)nregions * per);
+    const cudaError_t e2 = cudaMemcpyAsync(hred.data(), dred, hred.size() * sizeof(double),
+                                           cudaMemcpyDeviceToHost, st);
+    if (e2 != cudaSuccess) r = set_error(BL_ERR_CUDA, cudaGetErrorString(e2));
   }
   const cudaError_t es = cudaStreamSynchronize(st);
   if (r != BL_OK) return r;
   if (es != cudaSuccess) return set_error(BL_ERR_CUDA, cudaGetErrorString(es));
   *gamma_ref = L->plan.gamma_out;
   if (!want) return BL_OK;
-  unsigned long long nonfin = 0;
+  // each reduction point from the regions that computed it: in the chunked
+  // mode every chunk's; in the whole-bunch mode the head's or the tail's
+  // chunks, or the middle's single region
+  std::vector<int> grp_of_red((size_t)R, 0);
+  for (size_t g = 0; g < G; ++g)
+    if (red_of[g] >= 0) grp_of_red[red_of[g]] = (int)g;
   std::vector<double> pooled((size_t)R * 28);
-  std::vector<const double *> parts((size_t)nchunks);
+  std::vector<const double *> parts;
   for (int rr = 0; rr < R; ++rr) {
-    for (int64_t i = 0; i < nchunks; ++i)
-      parts[i] = hred.data() + (size_t)i * per + (size_t)rr * 28;
+    parts.clear();
+    const size_t g = (size_t)grp_of_red[rr];
+    if (!whole) {
+      for (int64_t i = 0; i < nchunks; ++i) parts.push_back(hred.data() + (size_t)i * per + (size_t)rr * 28);
+    } else if (g < h_end) {
+      for (int64_t i = 0; i < nchunks; ++i) parts.push_back(hred.data() + (size_t)i * per + (size_t)rr * 28);
+    } else if (g >= t_begin) {
+      for (int64_t i = 0; i < nchunks; ++i)
+        parts.push_back(hred.data() + (size_t)(nchunks + 1 + i) * per + (size_t)rr * 28);
+    } else {
+      parts.push_back(hred.data() + (size_t)nchunks * per + (size_t)rr * 28);
+    }
     pool_moments(parts, pooled.data() + (size_t)rr * 28);
   }
-  for (int64_t i = 0; i < nchunks; ++i) {
+  unsigned long long nonfin = 0;
+  for (int64_t k = 0; k < nregions; ++k) {
     unsigned long long c = 0;
-    std::memcpy(&c, hred.data() + (size_t)i * per + per - 1, sizeof(c));
+    std::memcpy(&c, hred.data() + (size_t)k * per + per - 1, sizeof(c));
     nonfin += c;
   }
   if (nonfinite_out) *nonfinite_out = (int64_t)nonfin;

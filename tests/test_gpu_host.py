@@ -25,10 +25,13 @@ def _bunch(n, seed):
     return [np.asarray(z[k], dtype=np.float32) for k in KEYS], g
 
 
-def _beamline(z):
+def _beamline(z, single_stage=False):
     """surrogate stage (with a training box that leaves ~10 % of the
     particles to the fallback pusher) + matching section + pusher stage +
-    matching section"""
+    matching section; single_stage: the surrogate stage and its section only
+    (bl_track_host then streams every chunk through the whole lattice
+    instead of keeping the bunch on the device between the first and the
+    last stage)"""
     from paper_2402_17248_gb300 import bl
     Z = np.stack(z, axis=1).astype(np.float64)
     mu, sd = np.nanmean(Z, axis=0), np.nanstd(Z, axis=0)
@@ -37,7 +40,9 @@ def _beamline(z):
     sur.set_domain(mu - 2.5 * sd, mu + 2.5 * sd)
     st = lattice.plasma(100)
     st["surrogate"] = sur
-    els = [st] + lattice.matching_section() + [lattice.plasma(100)] + lattice.matching_section()
+    els = [st] + lattice.matching_section()
+    if not single_stage:
+        els += [lattice.plasma(100)] + lattice.matching_section()
     return bl.Lattice(els), sur
 
 
@@ -69,12 +74,15 @@ def _moments_close(a, b):
     return np.all(err <= 2e-10)
 
 
-@pytest.mark.parametrize("n,chunk", [(300_001, 65536), (50_000, 0), (131_072, 32768)])
-def test_host_stream_matches_device(n, chunk):
+# (n, chunk, single-stage lattice): whole-bunch mode with a ragged last
+# chunk and with even chunks, one chunk, and the chunk-through mode
+@pytest.mark.parametrize("n,chunk,single", [(300_001, 65536, False), (131_072, 32768, False),
+                                            (50_000, 0, False), (300_001, 65536, True)])
+def test_host_stream_matches_device(n, chunk, single):
     import torch
     from paper_2402_17248_gb300 import bl
     z, g = _bunch(n, seed=21)
-    lat, _sur = _beamline(z)
+    lat, _sur = _beamline(z, single)
     want, m_dev, nf_dev, g_dev = _device_reference(z, g, lat)
     hin = [torch.from_numpy(c.copy()).pin_memory() for c in z]
     hout = [torch.empty(n, dtype=torch.float32).pin_memory() for _ in range(6)]
