@@ -124,7 +124,11 @@ bl_status run_segment(bl_bunch *b, bl_lattice_s *L, size_t g, bool moments, doub
   return BL_OK;
 }
 
-bl_status run_stage(bl_bunch *b, bl_lattice_s *L, size_t g, cudaStream_t st) {
+// fused: out-of-domain particles pushed by the surrogate kernel's fallback
+// warp (best when the launch is long); otherwise by the list pusher after it
+// (best for short launches on alternating streams, whose latency another
+// stream's work hides).
+bl_status run_stage(bl_bunch *b, bl_lattice_s *L, size_t g, cudaStream_t st, bool fused = true) {
   auto &P = L->plan;
   const bl_element &e = L->els[L->groups[g].first];
   const StageTrack &tr = P.stages[g];
@@ -148,10 +152,16 @@ bl_status run_stage(bl_bunch *b, bl_lattice_s *L, size_t g, cudaStream_t st) {
     dom.fb_count = (unsigned long long *)fb;
     dom.fb_list = (int64_t *)fb + 1;
     dom.fb_cap = b->n;
+    const float *tab = (const float *)((const uint8_t *)P.d_tables + P.table_off[g]);
+    dom.stage = consts_f(tr.c);
+    dom.table = tab;
+    dom.fused = fused ? 1 : 0;
     BL_CUDA(cudaMemsetAsync(dom.fb_count, 0, sizeof(unsigned long long), st));
+    // the surrogate kernel pushes the particles outside the domain itself
+    // (a fallback warp per CTA); the list pusher takes those past a CTA's
+    // queue, and exits at once when there are none
     BL_CUDA(launch_mlp_forward(soa_of<float>(b), b->n, s->img, s->nrm, ctx->num_sms,
                                ctx->err_word, st, &dom));
-    const float *tab = (const float *)((const uint8_t *)P.d_tables + P.table_off[g]);
     BL_CUDA(launch_pusher_list(soa_of<float>(b), dom.fb_list, dom.fb_count, b->n, tr.c, tab,
                                ctx->num_sms, st));
   } else if (e.surrogate) {
@@ -198,7 +208,7 @@ bl_status track_checks(bl_bunch *b, bl_lattice_s *L) {
 // bunch per reduction point, at the point's index) go into mom_dev and their
 // non-finite count into *nf (zeroed first) when mom_dev != NULL.
 bl_status track_enqueue_range(bl_bunch *b, bl_lattice_s *L, size_t g0, size_t g1, double *mom_dev,
-                              unsigned long long *nf, cudaStream_t st) {
+                              unsigned long long *nf, cudaStream_t st, bool fused_fallback = true) {
   std::vector<int> red_of;
   reduction_points(L, &red_of);
   const size_t per = (size_t)b->n_bunch * 28;
@@ -212,7 +222,7 @@ bl_status track_enqueue_range(bl_bunch *b, bl_lattice_s *L, size_t g0, size_t g1
                                                                                : "bl stage: pusher"));
     bl_status r = BL_OK;
     if (stage) {
-      r = run_stage(b, L, g, st);
+      r = run_stage(b, L, g, st, fused_fallback);
       if (r == BL_OK && want && red_of[g] >= 0) r = moments_device(b, mom_dev + red_of[g] * per, nf, st);
     } else if (b->dtype == BL_F32) {
       r = run_segment<float>(b, L, g, want, want ? mom_dev + red_of[g] * per : nullptr, nf, st);
@@ -540,7 +550,7 @@ bl_status bl_track_host(const float *const in_host[6], float *const out_host[6],
       if (e != cudaSuccess) break;
       bl_bunch v = view(dbuf, n, off, cn);
       r = track_checks(&v, L);
-      if (r == BL_OK) r = track_enqueue_range(&v, L, 0, h_end, region(i), region_nf(i), cs);
+      if (r == BL_OK) r = track_enqueue_range(&v, L, 0, h_end, region(i), region_nf(i), cs, false);
     }
     // the groups in between, once, on the whole bunch
     if (r == BL_OK && e == cudaSuccess) e = link(ctx->hp_comp[1], ctx->hp_comp[0], ev[EV_IN + 1]);
@@ -556,7 +566,7 @@ bl_status bl_track_host(const float *const in_host[6], float *const out_host[6],
       const int64_t off = i * chunk, cn = std::min(chunk, n - off);
       bl_bunch v = view(dbuf, n, off, cn);
       r = track_enqueue_range(&v, L, t_begin, G, region(nchunks + 1 + i),
-                              region_nf(nchunks + 1 + i), cs);
+                              region_nf(nchunks + 1 + i), cs, false);
       if (r == BL_OK) e = link(cs, d2h, ev[EV_TRACKED]);
       if (r == BL_OK && e == cudaSuccess) e = copies(dbuf, n, nullptr, off, cn, false, d2h);
     }
@@ -577,7 +587,7 @@ bl_status bl_track_host(const float *const in_host[6], float *const out_host[6],
       if (e != cudaSuccess) break;
       bl_bunch v = view(d, chunk, 0, cn);
       r = track_checks(&v, L);
-      if (r == BL_OK) r = track_enqueue_range(&v, L, 0, G, region(i), region_nf(i), cs);
+      if (r == BL_OK) r = track_enqueue_range(&v, L, 0, G, region(i), region_nf(i), cs, false);
       if (r != BL_OK) break;
       e = link(cs, d2h, ev[EV_TRACKED + b]);
       for (int c = 0; c < 6 && e == cudaSuccess; ++c)

@@ -45,6 +45,13 @@ struct StageConsts {
   double uz_ref_out;
   int nsteps;
 };
+// The stage constants in FP32 for the FP32 pusher (push_f32.cuh).
+struct ConstsF {
+  float kp, g, K0, h, h2, h6;
+  float bg_in, gamma_in, bg_out, gamma_out, uz_out;
+  int nsteps;
+};
+ConstsF consts_f(const StageConsts &c);
 // table: nsteps*4 entries of 4 values (T), see pusher.cu for the layout.
 template <typename T>
 cudaError_t launch_pusher(Soa<T> z, int64_t n, const StageConsts &c, const T *table,
@@ -85,13 +92,19 @@ struct MlpNormF { float mu_in[6][2], inv_sd_in[6][2], mu_out[6][2], sd_out[6][2]
 cudaError_t launch_mlp_pack(const float *params, uint8_t *img, float *bias, float *wt,
                             float *wn, cudaStream_t st);
 // err: device word that receives BL_DEVERR_* flags of bounded waits.
-// Training-input box of a surrogate; particles outside it are not mapped:
-// their indices go to fb_list (fb_count counts them) for the plain pusher.
+// Training-input box of a surrogate; particles outside it are not mapped
+// but pushed by the plain FP32 pusher of the stage (constants stage, RK4
+// reference table `table`): by the surrogate kernel's own fallback warp,
+// or, past its per-CTA queue, listed in fb_list (fb_count counts them) for
+// launch_pusher_list.
 struct MlpDomain {
   float lo[6], hi[6];
   int64_t *fb_list;
   unsigned long long *fb_count;
   int64_t fb_cap;
+  ConstsF stage;
+  const float *table;
+  int fused;  // 1: the fallback warp pushes (up to its queue); 0: every particle goes to the list
 };
 cudaError_t launch_mlp_forward(Soa<float> z, int64_t n, const uint8_t *img, const MlpNorm &nrm,
                                int num_sms, unsigned *err, cudaStream_t st,

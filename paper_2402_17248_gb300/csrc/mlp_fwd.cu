@@ -37,6 +37,7 @@
 //    FP32 pipes. A slot's next inputs are loaded from HBM while the current
 //    tile is in the network.
 #include "mlp_common.cuh"
+#include "push_f32.cuh"
 
 namespace bl {
 
@@ -49,15 +50,23 @@ constexpr int WG_PER_SLOT = 2;                     // epilogue warpgroups per sl
 constexpr int FEAT_WG = 128 / WG_PER_SLOT;         // hidden features per warpgroup
 constexpr int CHUNK = 16;                          // accumulator columns per tcgen05.ld
 constexpr int EPI_THREADS = 128 * WG_PER_SLOT * SLOTS;
-constexpr int THREADS = EPI_THREADS + 32;          // + the MMA warp
-constexpr int MMA_WARP = EPI_THREADS / 32;
+constexpr int EPI_WARPS = EPI_THREADS / 32;
+constexpr int THREADS = EPI_THREADS + 64;          // + the MMA warp + the fallback warp
+constexpr int MMA_WARP = EPI_WARPS;
+constexpr int FB_WARP = EPI_WARPS + 1;
 constexpr uint32_t ACT_BYTES = 128 * 128 * 2;      // one slot's BF16 activations
 constexpr uint32_t OFF_ACT = (MLP_IMG_BYTES + 1023) / 1024 * 1024;
 constexpr uint32_t OFF_ONES = OFF_ACT + SLOTS * ACT_BYTES;  // 128 x 16 BF16 A matrix
 constexpr uint32_t ONES_BYTES = 128 * 16 * 2;
 constexpr uint32_t OFF_BAR = OFF_ONES + ONES_BYTES;  // 1 weights + 3 mma-done + 3 epi-done
 constexpr uint32_t OFF_SLOT = OFF_BAR + 8 * (1 + 2 * SLOTS);
-constexpr uint32_t SMEM_BYTES = (OFF_SLOT + 4 + 127) / 128 * 128;
+// fallback queue: indices of this CTA's particles outside the training
+// domain (-1 until written), then [0] the queue tail, [1] the number of
+// epilogue warps that have finished all their tiles
+constexpr int FBQ_CAP = 256;
+constexpr uint32_t OFF_FBQ = (OFF_SLOT + 4 + 15) / 16 * 16;
+constexpr uint32_t OFF_FBC = OFF_FBQ + FBQ_CAP * 8;
+constexpr uint32_t SMEM_BYTES = (OFF_FBC + 8 + 127) / 128 * 128;
 static_assert(SMEM_BYTES <= 227 * 1024, "shared memory budget");
 static_assert(SMEM_BYTES > 114 * 1024, "one CTA per SM (it owns all tensor memory)");
 // Tensor memory: 128 FP32 accumulator columns per slot.
@@ -133,6 +142,13 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
   // core matrices (8 rows x 16 bytes, K chunks 128 bytes apart, row groups
   // 256 bytes apart)
   init_ones(smem, OFF_ONES, tid, THREADS);
+  long long *fbq = reinterpret_cast<long long *>(smem + OFF_FBQ);
+  int *fbc = reinterpret_cast<int *>(smem + OFF_FBC);
+  for (int i = tid; i < FBQ_CAP; i += THREADS) fbq[i] = -1;
+  if (tid == 0) {
+    fbc[0] = 0;
+    fbc[1] = 0;
+  }
   tc::fence_proxy_async();
   tc::fence_before();
   __syncthreads();
@@ -196,6 +212,50 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
       }
     }
     __syncwarp();
+  } else if (warp == FB_WARP) {
+    // ------------------------------------------------------- fallback warp
+    // Pushes this CTA's particles outside the training domain through the
+    // stage with the plain FP32 pusher, 32 at a time (one per lane), while
+    // the tensor pipeline goes on with the other tiles. The epilogue queues
+    // a particle when it reads the particle's input; the warp leaves once
+    // every epilogue warp has finished its tiles and the queue is drained.
+    // Every wait is bounded.
+    if (dom.fb_list && dom.fused) {
+      volatile long long *vq = fbq;
+      volatile int *vc = fbc;
+      const float4 *table = reinterpret_cast<const float4 *>(dom.table);
+      int head = 0;
+      uint32_t idle = 0;
+      for (;;) {
+        int tail = 0, fin = 0;
+        if (lane == 0) {
+          fin = vc[1];  // read before the tail: a finished warp has queued everything
+          tail = min(vc[0], FBQ_CAP);
+        }
+        tail = __shfl_sync(0xffffffffu, tail, 0);
+        fin = __shfl_sync(0xffffffffu, fin, 0);
+        if (head < tail) {
+          const int k = head + lane;
+          if (k < tail) {
+            // the entry is written right after its slot is reserved
+            long long p = vq[k];
+            for (uint32_t w = 0; p < 0 && w < (1u << 22); ++w) p = vq[k];
+            if (p >= 0) push::push_particle(z, p, dom.stage, table);
+            else atomicOr(err, BL_DEVERR_BARRIER_TIMEOUT);
+          }
+          __syncwarp();
+          head = min(tail, head + 32);
+          idle = 0;
+          continue;
+        }
+        if (fin == EPI_WARPS) break;  // nothing queued after the finish count was read
+        if (++idle > (1u << 26)) {    // ~30 s of polling: give up and flag it
+          if (lane == 0) atomicOr(err, BL_DEVERR_BARRIER_TIMEOUT);
+          break;
+        }
+        __nanosleep(256);
+      }
+    }
   } else {
     // ------------------------------------------------------ epilogue warps
     const int wg = warp >> 2, wq = warp & 3;
@@ -230,12 +290,24 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
     for (; ok && tile < ntiles; tile += tstride) {
       const int64_t p = tile * 128 + m;
       const bool valid = p < n;
-      // outside the training-input box: left unchanged and listed for the
-      // plain pusher (a NaN compares false and is mapped, so it stays visible)
+      // outside the training-input box: not mapped, but pushed by the plain
+      // pusher (a NaN compares false and is mapped, so it stays visible)
       bool outside = false;
       if (dom.fb_list) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) outside |= (xin[c] < dom.lo[c]) | (xin[c] > dom.hi[c]);
+        if (io && valid && outside) {
+          // to this CTA's fallback warp, or, past its queue, to the global
+          // list for the separate list-mode pusher
+          const int k = dom.fused ? atomicAdd(&fbc[0], 1) : FBQ_CAP;
+          if (k < FBQ_CAP) {
+            reinterpret_cast<volatile long long *>(fbq)[k] = p;
+          } else {
+            const unsigned long long g = atomicAdd(dom.fb_count, 1ull);
+            if ((int64_t)g < dom.fb_cap) dom.fb_list[g] = p;
+            else outside = false;  // list full (cannot happen with capacity n): keep the map
+          }
+        }
       }
       if (io) {  // normalised BF16 input row; bias hi/lo columns k = 6, 7; k = 8..15 zero
         float xn[6];
@@ -282,18 +354,17 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
       uint32_t r[8];
       tc::tmem_ld8(t_acc, r);
       tc::tmem_ld_wait();
-      if (valid && outside) {
-        const unsigned long long k = atomicAdd(dom.fb_count, 1ull);
-        if ((int64_t)k < dom.fb_cap) dom.fb_list[k] = p;
-        else outside = false;  // list full (cannot happen with capacity n): keep the map
-      }
-      if (valid && !outside) {
+      if (valid && !outside) {  // particles outside the domain are the pushers'
 #pragma unroll
         for (int c = 0; c < 6; ++c)
           z.c[c][p] = df_affine(__uint_as_float(r[c]), nrm.sd_out[c][0], nrm.sd_out[c][1],
                                 nrm.mu_out[c][0], nrm.mu_out[c][1]);
       }
     }
+    // this warp has queued all its fallback particles
+    __syncwarp();
+    __threadfence_block();
+    if (lane == 0) atomicAdd(&fbc[1], 1);
   }
   tc::fence_before();
   __syncthreads();

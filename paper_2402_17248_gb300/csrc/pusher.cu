@@ -26,50 +26,13 @@
 // w at every stage (used for the small FP64 configuration).
 #include "common.cuh"
 #include "internal.h"
+#include "push_f32.cuh"
 
 namespace bl {
 
 namespace {
 
 struct alignas(32) D4 { double x, y, z, w; };
-
-struct ConstsF {
-  float kp, g, K0, h, h2, h6;
-  float bg_in, gamma_in, bg_out, gamma_out, uz_out;
-  int nsteps;
-};
-
-BL_DEV float rcp_approx(float x) {
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-
-struct StateF { float x, ux, y, uy, dz, du; };
-
-BL_DEV StateF eval_f(const StateF &Y, float uz_r, float w_r, float sphi, float cphi, float dcos,
-                     const ConstsF &c) {
-  const float uz = uz_r + Y.du;
-  const float q = fmaf(Y.uy, Y.uy, fmaf(Y.ux, Y.ux, 1.0f));
-  const float r = rcp_approx(uz);
-  const float a = q * r * r;
-  const float w = 0.5f * a * fmaf(-0.25f, a, 1.0f);
-  const float F = (1.0f + w) * c.K0 * sphi;
-  const float dw = w - w_r;
-  StateF k;
-  k.x = Y.ux * r;
-  k.ux = -F * Y.x;
-  k.y = Y.uy * r;
-  k.uy = -F * Y.y;
-  k.dz = -dw;
-  k.du = c.g * fmaf(dcos, 1.0f + w_r, dw * cphi);
-  return k;
-}
-
-BL_DEV StateF axpy(const StateF &Y, float a, const StateF &k) {
-  return {fmaf(a, k.x, Y.x), fmaf(a, k.ux, Y.ux), fmaf(a, k.y, Y.y),
-          fmaf(a, k.uy, Y.uy), fmaf(a, k.dz, Y.dz), fmaf(a, k.du, Y.du)};
-}
 
 // LIST: push only the particles list[0 .. min(*count, n)) (the surrogate's
 // fallback particles); otherwise every particle p < n.
@@ -79,80 +42,8 @@ pusher_f32(Soa<float> z, int64_t n, ConstsF c, const float4 *__restrict__ table,
            const int64_t *__restrict__ list, const unsigned long long *count) {
   const int64_t m = LIST ? min(n, (int64_t)*count) : n;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t p = LIST ? list[i] : i;
-    StateF Y;
-    {
-      const float x = z.c[0][p], px = z.c[1][p], y = z.c[2][p], py = z.c[3][p];
-      const float t = z.c[4][p], pt = z.c[5][p];
-      Y.x = x;
-      Y.y = y;
-      Y.ux = px * c.bg_in;
-      Y.uy = py * c.bg_in;
-      const float dg = -pt * c.bg_in;  // gamma - gamma_ref
-      const float up2 = fmaf(Y.uy, Y.uy, Y.ux * Y.ux);
-      const float gam = c.gamma_in + dg;
-      const float uz = sqrtf(fmaf(gam, gam, -1.0f - up2));
-      Y.du = fmaf(dg, gam + c.gamma_in, -up2) / (uz + c.bg_in);
-      Y.dz = -t;
-    }
-    for (int s = 0; s < c.nsteps; ++s) {
-      const float4 e0 = __ldg(table + 4 * s + 0);
-      const float4 e1 = __ldg(table + 4 * s + 1);
-      const float4 e2 = __ldg(table + 4 * s + 2);
-      const float4 e3 = __ldg(table + 4 * s + 3);
-      const float sr = e0.z, cr = e0.w;
-      float s2, c2;
-      sincosf(0.5f * c.kp * Y.dz, &s2, &c2);
-      const float sD = 2.0f * s2 * c2;
-      const float cm1 = -2.0f * s2 * s2;
-      const float sphi = fmaf(sr, cm1, fmaf(cr, sD, sr));
-      const float dcos = fmaf(cr, cm1, -sr * sD);
-      const float cphi = cr + dcos;
-      const float dsr = sphi - sr;
-      // stage 1
-      StateF k1 = eval_f(Y, e0.x, e0.y, sphi, cphi, dcos, c);
-      // stage 2
-      StateF Y2 = axpy(Y, c.h2, k1);
-      float dz = Y2.dz - Y.dz;
-      float eps = fmaf(c.kp, dz, e1.z);
-      StateF k2 = eval_f(Y2, e1.x, e1.y, fmaf(cphi, eps, sphi), fmaf(-sphi, eps, cphi),
-                         fmaf(-dsr, e1.z, fmaf(-sphi * c.kp, dz, dcos)), c);
-      // stage 3
-      StateF Y3 = axpy(Y, c.h2, k2);
-      dz = Y3.dz - Y.dz;
-      eps = fmaf(c.kp, dz, e2.z);
-      StateF k3 = eval_f(Y3, e2.x, e2.y, fmaf(cphi, eps, sphi), fmaf(-sphi, eps, cphi),
-                         fmaf(-dsr, e2.z, fmaf(-sphi * c.kp, dz, dcos)), c);
-      // stage 4
-      StateF Y4 = axpy(Y, c.h, k3);
-      dz = Y4.dz - Y.dz;
-      eps = fmaf(c.kp, dz, e3.z);
-      StateF k4 = eval_f(Y4, e3.x, e3.y, fmaf(cphi, eps, sphi), fmaf(-sphi, eps, cphi),
-                         fmaf(-dsr, e3.z, fmaf(-sphi * c.kp, dz, dcos)), c);
-      StateF acc;
-      acc.x = k1.x + 2.0f * (k2.x + k3.x) + k4.x;
-      acc.ux = k1.ux + 2.0f * (k2.ux + k3.ux) + k4.ux;
-      acc.y = k1.y + 2.0f * (k2.y + k3.y) + k4.y;
-      acc.uy = k1.uy + 2.0f * (k2.uy + k3.uy) + k4.uy;
-      acc.dz = k1.dz + 2.0f * (k2.dz + k3.dz) + k4.dz;
-      acc.du = k1.du + 2.0f * (k2.du + k3.du) + k4.du;
-      Y = axpy(Y, c.h6, acc);
-    }
-    {
-      const float uz = c.uz_out + Y.du;
-      const float up2 = fmaf(Y.uy, Y.uy, Y.ux * Y.ux);
-      const float gam = sqrtf(fmaf(uz, uz, 1.0f + up2));
-      const float dg = fmaf(Y.du, uz + c.uz_out, up2) / (gam + c.gamma_out);
-      const float ib = 1.0f / c.bg_out;
-      z.c[0][p] = Y.x;
-      z.c[1][p] = Y.ux * ib;
-      z.c[2][p] = Y.y;
-      z.c[3][p] = Y.uy * ib;
-      z.c[4][p] = -Y.dz;
-      z.c[5][p] = -dg * ib;
-    }
-  }
+       i += (int64_t)gridDim.x * blockDim.x)
+    push::push_particle(z, LIST ? list[i] : i, c, table);
 }
 
 // ---------------------------------------------------------------- FP64 ----
@@ -234,7 +125,7 @@ pusher_f64(Soa<double> z, int64_t n, StageConsts c, const D4 *__restrict__ table
 
 }  // namespace
 
-static ConstsF consts_f(const StageConsts &c) {
+ConstsF consts_f(const StageConsts &c) {
   ConstsF f;
   f.kp = (float)c.kp;
   f.g = (float)c.g;

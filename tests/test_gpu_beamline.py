@@ -329,3 +329,48 @@ def test_trained_surrogate_gain_over_pusher():
     assert tp / ts > 5
     assert info["test_loss"] < 0.05
     assert err["rel_energy_spread"] < 0.05
+
+
+@pytest.mark.parametrize("width", [3.5, 2.0, 0.7])
+def test_fused_fallback_equals_plain_pusher(width):
+    """Particles outside a surrogate's training box are pushed inside the
+    surrogate kernel by its fallback warp (past a CTA's 256-entry queue, by
+    the list-mode pusher) with the plain FP32 pusher's arithmetic, so they
+    equal bl_push_stage's result bit for bit; the others equal the
+    domain-free network's output. Box half-widths of 3.5, 2 and 0.7 sigma
+    put ~0.3 %, ~25 % and ~98 % of a 10^6-particle bunch outside: the queue
+    alone, the queue plus the list, and nearly all through the list."""
+    from paper_2402_17248_gb300 import bl
+    n = 1_000_000
+    z, g = _bunch(n, seed=31)
+    Z = np.stack(z, axis=1)
+    mu, sd = Z.mean(axis=0), Z.std(axis=0)
+    Ws, bs = mlp_init(WIDTHS, 7)
+    sur = bl.Surrogate(Ws, bs, mu, sd, mu, sd)
+    sur.set_domain(mu - width * sd, mu + width * sd)
+    # the FP32 box the kernel compares with (the library widens the FP64
+    # bounds outward to FP32)
+    import ctypes
+    lo64, hi64, has = np.zeros(6), np.zeros(6), ctypes.c_int32(0)
+    assert bl.lib().bl_surrogate_get_domain(sur.handle, lo64.ctypes.data, hi64.ctypes.data,
+                                            ctypes.byref(has)) == bl.BL_OK and has.value
+    lo, hi = lo64.astype(np.float32), hi64.astype(np.float32)
+    z32 = np.stack([np.asarray(c, dtype=np.float32) for c in z])
+    inside = np.all((z32 >= lo[:, None]) & (z32 <= hi[:, None]), axis=0)
+    st = lattice.plasma(400)
+    st["surrogate"] = sur
+    b1 = to_bunch(z, g)
+    bl.bl_track(b1, bl.Lattice([st]), moments=False)
+    got = from_bunch(b1)
+    b2 = to_bunch(z, g)
+    bl.bl_push_stage(b2, lattice.plasma(400))
+    push = from_bunch(b2)
+    sur.set_domain(None, None)
+    b3 = to_bunch(z, g)
+    bl.bl_track(b3, bl.Lattice([st]), moments=False)
+    net = from_bunch(b3)
+    print("box +-%.1f sigma: %.4f of the particles outside" % (width, 1.0 - inside.mean()))
+    assert 0 < (~inside).sum() < n
+    for a, p_, q in zip(got, push, net):
+        assert np.array_equal(a[~inside], p_[~inside])
+        assert np.array_equal(a[inside], q[inside])
