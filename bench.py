@@ -39,7 +39,7 @@ SEG_BYTES_PER_PARTICLE = 48
 # DRAM bytes (read + write) per particle of mlp_forward_kernel from one ncu
 # capture of the current kernel on 8,388,608 particles (201.6 MB + 139.6 MB),
 # scaled per particle; see profiles/mlp_forward_kernel_8M_particles.md
-MLP_DRAM_BYTES_PER_PARTICLE = (201.623296e6 + 139.620352e6) / 8388608
+MLP_DRAM_BYTES_PER_PARTICLE = (201.568768e6 + 139.784192e6) / 8388608
 KEYS = ("x", "px", "y", "py", "t", "pt")
 
 
