@@ -37,7 +37,7 @@ STEPS_PER_STAGE = 400
 FLOP_PER_PARTICLE_STAGE = 2 * (6 * 128 + 3 * 128 * 128 + 128 * 6)  # 101,376
 SEG_BYTES_PER_PARTICLE = 48
 # DRAM bytes (read + write) per particle of mlp_forward_kernel from one ncu
-# capture of the current kernel on 8,388,608 particles (201.6 MB + 139.6 MB),
+# capture of the current kernel on 8,388,608 particles (201.6 MB + 139.8 MB),
 # scaled per particle; see profiles/mlp_forward_kernel_8M_particles.md
 MLP_DRAM_BYTES_PER_PARTICLE = (201.568768e6 + 139.784192e6) / 8388608
 KEYS = ("x", "px", "y", "py", "t", "pt")
