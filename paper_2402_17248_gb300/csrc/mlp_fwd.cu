@@ -4,7 +4,7 @@
 // particles, with the normalise / de-normalise data preparation fused).
 //
 // Design (one persistent CTA per SM, three 128-particle tile slots per CTA,
-// warp-specialised):
+// warp-specialised: 24 epilogue warps, an MMA-issuing warp, a fallback warp):
 //  * The weight matrices and bias blocks (BF16, ~117 KB) are copied once per
 //    CTA into shared memory by bulk async copies and stay there for all
 //    tiles. They are the B operand of every MMA, in the K-major no-swizzle
@@ -36,6 +36,11 @@
 //    carries about 44 bits, i.e. FP64-grade constants and rounding, on the
 //    FP32 pipes. A slot's next inputs are loaded from HBM while the current
 //    tile is in the network.
+//  * With a training domain, a particle outside it is not mapped: the
+//    epilogue queues it when it reads the input, and a fallback warp of the
+//    CTA pushes it through the stage with the plain FP32 pusher
+//    (push_f32.cuh) while the tensor pipeline goes on; a full queue spills
+//    into a global list for the separate list-mode pusher.
 #include "mlp_common.cuh"
 #include "push_f32.cuh"
 
@@ -111,8 +116,8 @@ BL_DEV void gelu_chunk(const uint32_t (&r)[CH], uint32_t row, int f0) {
 }
 
 // Registers: the 4 sub-partitions of the SM each hold a quarter of the 64K
-// registers, and warp w runs on sub-partition w % 4, so the MMA warp makes
-// sub-partition 0 host one warp more than the others.
+// registers, and warp w runs on sub-partition w % 4, so the MMA and fallback
+// warps make sub-partitions 0 and 1 host one warp more than the others.
 constexpr int WARPS_SMSP0 = (THREADS / 32 + 3) / 4;
 constexpr int MAX_REGS = (16384 / (32 * WARPS_SMSP0)) / 8 * 8;
 
