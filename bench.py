@@ -215,6 +215,27 @@ def side_measurements(args, bl, workflow, lattice, surs, infos, z0, g, elements,
     out["training"] = {"samples_per_s": steps * args.train_batch / secs, "batch": args.train_batch,
                        "steps": steps, "seconds": secs,
                        "kernels": "mlp_train_tc_kernel + reduce_adam_kernel + mlp_pack_kernel per step"}
+    # the paper's minibatch (1200 pairs, 9.4 tiles of 128): steps of a scratch
+    # surrogate on 2^20 random pairs, CUDA events around 280 steps
+    from synth.bunch import mlp_init
+    Wt, bt = mlp_init([6, 128, 128, 128, 128, 6], 1)
+    scratch = bl.Surrogate(Wt, bt, np.zeros(6), np.ones(6), np.zeros(6), np.ones(6))
+    gen = torch.Generator(device=dev).manual_seed(0)
+    pin = torch.randn(6, 1 << 20, device=dev, generator=gen)
+    pout = torch.randn(6, 1 << 20, device=dev, generator=gen)
+    pidx = torch.randint(0, 1 << 20, (300, 1200), device=dev, generator=gen)
+    for j in range(20):
+        bl.bl_surrogate_train_step(scratch, pin, pout, idx=pidx[j], batch=1200, lr=1e-4)
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for j in range(20, 300):
+        bl.bl_surrogate_train_step(scratch, pin, pout, idx=pidx[j], batch=1200, lr=1e-4)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    us = ev[0].elapsed_time(ev[1]) * 1e3 / 280
+    out["training"]["paper_batch"] = {"batch": 1200, "us_per_step": us,
+                                      "samples_per_s": 1200 / (us * 1e-6)}
+    del scratch, pin, pout, pidx
 
     # batched: 256 bunches with log-uniform counts in [1e4, 1e6] and 32 quad
     # strengths each (magnitudes U[20, 80], signs -,+,-,+), stored back to
