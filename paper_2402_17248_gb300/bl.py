@@ -102,6 +102,7 @@ _SIGS = {
     "bl_poll_device_errors": ([], C.c_int),
     "bl_debug_fail_allocations": ([C.c_int], C.c_int),
     "bl_debug_train_kernel": ([C.c_int], C.c_int),
+    "bl_debug_pool_moments": ([_P, C.c_int32, _P], C.c_int),
     "bl_debug_umma_probe": ([_P, _P, _P, C.c_int, C.c_int, C.c_uint32, C.c_uint32,
                              C.c_uint32, C.c_uint32, _P], C.c_int),
 }

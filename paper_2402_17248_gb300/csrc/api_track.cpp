@@ -763,3 +763,13 @@ bl_status bl_push_stage(bl_bunch *b, const bl_element *stage, bl_stream stream) 
 }
 
 }  // extern "C"
+
+// Diagnostic entry point (declared in include/bl_debug.h): the FP64 pooling
+// that bl_track_host applies to chunked moment reductions.
+extern "C" int bl_debug_pool_moments(const double *parts, int32_t k, double *out) {
+  if (!parts || !out || k < 1) return 1;
+  std::vector<const double *> v((size_t)k);
+  for (int32_t i = 0; i < k; ++i) v[i] = parts + (size_t)i * 28;
+  pool_moments(v, out);
+  return 0;
+}

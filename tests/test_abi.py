@@ -156,3 +156,38 @@ def test_track_host_validation_before_any_work():
     assert e.value.status == bl.BL_ERR_INVALID_ARG
     with pytest.raises(ValueError):
         bl.bl_track_host(a, [np.zeros(8, dtype=np.float64)] * 6, 2000.0, L, stream=0)
+
+
+def _moments28(Z):
+    """[N, 6 means, 21 central second moments (1/N), a <= b row by row]"""
+    out = np.zeros(28)
+    if len(Z) == 0:
+        return out
+    mu = Z.mean(axis=0)
+    C = (Z - mu).T @ (Z - mu) / len(Z)
+    out[0], out[1:7] = len(Z), mu
+    out[7:] = [C[a, b] for a in range(6) for b in range(a, 6)]
+    return out
+
+
+def test_pool_moments_equals_moments_of_the_union():
+    """The FP64 pooling bl_track_host applies to chunked reductions (host code
+    of the library) equals the moments of the union computed directly: the
+    chunks have different sizes (one empty), offsets of several sigma and
+    different spreads, so a missing or wrong parallel-axis term fails."""
+    rng = np.random.default_rng(5)
+    sizes = [1, 7, 1000, 0, 123457, 4096]
+    chunks = [rng.normal(loc=3.0 * rng.normal(size=6), scale=rng.uniform(0.5, 2.0, size=6),
+                         size=(m, 6)) for m in sizes]
+    parts = np.ascontiguousarray(np.stack([_moments28(c) for c in chunks]))
+    out = np.zeros(28)
+    assert bl.lib().bl_debug_pool_moments(parts.ctypes.data, len(sizes), out.ctypes.data) == 0
+    want = _moments28(np.concatenate(chunks))
+    sd = np.sqrt(want[[7, 13, 18, 22, 25, 27]])
+    scale = np.concatenate([[want[0]], sd, [sd[a] * sd[b] for a in range(6) for b in range(a, 6)]])
+    assert np.max(np.abs(out - want) / scale) < 1e-12
+    # one set pools to itself; bad arguments are refused
+    one = np.zeros(28)
+    assert bl.lib().bl_debug_pool_moments(parts[2].ctypes.data, 1, one.ctypes.data) == 0
+    assert np.allclose(one, parts[2], rtol=1e-15, atol=0.0)
+    assert bl.lib().bl_debug_pool_moments(parts.ctypes.data, 0, out.ctypes.data) == 1
