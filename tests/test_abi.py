@@ -191,3 +191,26 @@ def test_pool_moments_equals_moments_of_the_union():
     assert bl.lib().bl_debug_pool_moments(parts[2].ctypes.data, 1, one.ctypes.data) == 0
     assert np.allclose(one, parts[2], rtol=1e-15, atol=0.0)
     assert bl.lib().bl_debug_pool_moments(parts.ctypes.data, 0, out.ctypes.data) == 1
+
+
+def _prototypes():
+    """name -> number of parameters of every function declared in include/*.h"""
+    protos = {}
+    for h in ("bl.h", "bl_debug.h"):
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        for m in re.finditer(r"\b(bl_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", src):
+            params = m.group(2).strip()
+            protos[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return protos
+
+
+def test_binding_arity_matches_the_header():
+    """every function the header declares is bound in bl.py with the same
+    number of arguments (a mismatch would silently shift arguments)"""
+    protos = _prototypes()
+    assert len(protos) >= 20
+    for name, n in protos.items():
+        assert name in bl._SIGS, name
+        assert len(bl._SIGS[name][0]) == n, (name, len(bl._SIGS[name][0]), n)
