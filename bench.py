@@ -36,15 +36,32 @@ N_STAGES = 8
 STEPS_PER_STAGE = 400
 FLOP_PER_PARTICLE_STAGE = 2 * (6 * 128 + 3 * 128 * 128 + 128 * 6)  # 101,376
 SEG_BYTES_PER_PARTICLE = 48
-# DRAM bytes (read + write) per particle of mlp_forward_kernel from one ncu
-# capture of the current kernel on 8,388,608 particles (201.6 MB + 139.8 MB),
-# scaled per particle; see profiles/mlp_forward_kernel_8M_particles.md
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one
+# mlp_forward_kernel launch on 8,388,608 particles in one ncu capture of the
+# current kernel (201.6 MB + 139.8 MB), scaled per particle to the launch size
 MLP_DRAM_BYTES_PER_PARTICLE = (201.568768e6 + 139.784192e6) / 8388608
+MLP_DRAM_BASIS = "ncu dram bytes of one launch on 2^23 particles, scaled by the particle count"
+# algorithmic flop per particle-stage of a whole gradient: the forward
+# surrogate pass plus the VJP (forward recomputation and reverse sweep)
+ADJOINT_FLOP_PER_PARTICLE_STAGE = 3 * FLOP_PER_PARTICLE_STAGE
 KEYS = ("x", "px", "y", "py", "t", "pt")
 
 
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
+
+
+def load_peaks():
+    """Roofline denominators: the measured copy bandwidth and BF16 GEMM rates
+    of this GPU model (MEASURED_PEAKS.json at the repository root), else the
+    fallback figures of one earlier GB300 measurement."""
+    try:
+        p = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return {"bf16": p.get("bf16_tflops", 1900.0),
+                "bf16_sustained": p.get("bf16_tflops_sustained", 1700.0),
+                "hbm": p.get("hbm_gbs", 6800.0), "source": "measured"}
+    except (OSError, ValueError):
+        return {"bf16": 1900.0, "bf16_sustained": 1700.0, "hbm": 6800.0, "source": "fallback"}
 
 
 def parse():
@@ -86,7 +103,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -323,15 +340,26 @@ def side_measurements(args, bl, workflow, lattice, surs, infos, z0, g, elements,
     step_a()
     torch.cuda.synchronize()
     ka = 3
-    t = time.perf_counter()
+    ev[0].record(stream)
     for _ in range(ka):
         J, grad = step_a()
+    ev[1].record(stream)
     torch.cuda.synchronize()
-    a_ms = 1e3 * (time.perf_counter() - t) / ka
+    a_ms = ev[0].elapsed_time(ev[1]) / ka
+    a_tflops = ADJOINT_FLOP_PER_PARTICLE_STAGE * na * N_STAGES / (a_ms * 1e-3) / 1e12
+    pk = load_peaks()
     out["adjoint"] = {"value": na * N_STAGES / (a_ms * 1e-3), "unit": "particle-stages/s",
                       "ms_per_gradient": a_ms, "particles": na, "quads": int(grad.shape[1]),
                       "objective": "eps_n_x", "J": float(J[0]),
-                      "timing": "host wall clock per bl_track_grad call (it returns host values)"}
+                      "timing": "CUDA events on the stream around each bl_track_grad call (the "
+                                "call synchronises twice to read moments and dJ/dk)",
+                      "roofline": {"bound": "tensor", "achieved": a_tflops,
+                                   "peak": pk["bf16_sustained"], "unit": "TFLOP/s",
+                                   "frac": a_tflops / pk["bf16_sustained"],
+                                   "peak_source": pk["source"] + " bf16 sustained",
+                                   "flop_per_particle_stage": ADJOINT_FLOP_PER_PARTICLE_STAGE,
+                                   "kernels": "8 mlp_forward + 8 mlp_vjp + segment maps and "
+                                              "transposes per gradient"}}
     del za, za0, ba
     torch.cuda.empty_cache()
 
@@ -373,10 +401,7 @@ def paper_networks(bl, npw, g, dev):
                      "tflops_algorithmic": flop * npw / (ms * 1e-3) / 1e12,
                      "paper_A100_ns_per_particle_stage": paper_ns})
         del net
-    try:
-        peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("bf16_tflops", 1900.0)
-    except OSError:
-        peak = 1900.0
+    peak = load_peaks()["bf16"]
     for r in rows:
         r["frac_of_bf16_peak"] = r["tflops_algorithmic"] / peak
     return rows
@@ -408,34 +433,21 @@ def main():
               flush=True)
         return 0
     from synth import lattice
-    from synth.bunch import BunchRecipe, gaussian_bunch, training_population
+    from synth.bunch import BunchRecipe, gaussian_bunch
 
     t_setup = time.time()
     n = args.particles
-    # ---- training data from the plain pusher over a randomised population
-    kp = math.sqrt(1e17 * 1e6 * 1.602176634e-19 ** 2 / (8.8541878128e-12 * 9.1093837015e-31)) / 299792458.0
+    # ---- training data from the plain pusher over a randomised population,
+    # then one network per stage (held-out loss every 5000 steps at the
+    # defaults, for the time to the loss plateau)
     g0 = BunchRecipe().gamma_ref
-    per = 65536
-    nb = max(1, args.train_pairs // per)
-    zt, _ = training_population(nb, per, g0, 0.2 / kp, seed=1000)
-    tb = workflow.device_bunch(zt, g0)
     elements = lattice.staged_beamline(N_STAGES, STEPS_PER_STAGE)
-    pairs = workflow.stage_pairs(tb, elements)
-    del tb
-    log("training pairs ready: %d stages x %d pairs (%.1fs)" % (len(pairs), nb * per, time.time() - t_setup))
-    surs, infos = [], []
-    for s, (xin, xout, gin) in enumerate(pairs):
-        # held-out loss every 5000 steps (24 evaluations at the defaults), for
-        # the time to the loss plateau
-        sur, info = workflow.fit_surrogate(xin, xout, steps=args.train_steps, batch=args.train_batch,
-                                           lr=args.train_lr, seed=100 + s, t_scale=args.train_t_scale,
-                                           log_every=5)
-        surs.append(sur)
-        infos.append(info)
-        log("stage %d surrogate: test loss %.3e after %d steps (%.1fs)" %
-            (s + 1, info["test_loss"], info["steps"], info["seconds"]))
-    del pairs
-    torch.cuda.empty_cache()
+    surs, infos = workflow.train_beamline_surrogates(
+        elements, g0, pairs_per_stage=args.train_pairs, steps=args.train_steps,
+        batch=args.train_batch, lr=args.train_lr, t_scale=args.train_t_scale, log_every=5,
+        log=log)
+    nb, per = infos[0]["pairs"] // 65536, 65536
+    log("training done (%.1fs)" % (time.time() - t_setup))
 
     # ---- the tracked bunch: rank r tracks particles [r n, (r+1) n) of one
     # world*n-particle bunch (weak scaling, no exchange in the data path)
@@ -516,9 +528,22 @@ def main():
     torch.cuda.synchronize()
     mlp_ms = ev[0].elapsed_time(ev[1]) / reps
     mlp_tflops = FLOP_PER_PARTICLE_STAGE * n / (mlp_ms * 1e-3) / 1e12
-    # the HBM-bound segment map alone (one fused 17-element section, no
-    # moments), launched through a lattice whose device plan is cached
+    # the HBM-bound segment pass the step runs: one fused 17-element section
+    # map with the moment reduction at its entry (and its finalize), enqueued
+    # through bl_track_async on a lattice whose device plan is cached
     lat_seg = bl.Lattice(lattice.matching_section())
+    red_seg = torch.zeros(bl.reduced_size(lat_seg, bunch), dtype=torch.float64, device=dev)
+    restore()
+    bl.bl_track_async(bunch, lat_seg, red_seg)
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(reps):
+        bl.bl_track_async(bunch, lat_seg, red_seg)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    seg_ms = ev[0].elapsed_time(ev[1]) / reps
+    seg_gbs = SEG_BYTES_PER_PARTICLE * n / (seg_ms * 1e-3) / 1e9
+    # and the map alone (no moments), for comparison
     restore()
     bl.bl_track(bunch, lat_seg, moments=False)
     torch.cuda.synchronize()
@@ -527,8 +552,7 @@ def main():
         bl.bl_track(bunch, lat_seg, moments=False)
     ev[1].record(stream)
     torch.cuda.synchronize()
-    seg_ms = ev[0].elapsed_time(ev[1]) / reps
-    seg_gbs = SEG_BYTES_PER_PARTICLE * n / (seg_ms * 1e-3) / 1e9
+    map_ms = ev[0].elapsed_time(ev[1]) / reps
 
     # ---- the plain FP32 pusher beamline on the same bunch
     restore()
@@ -579,14 +603,8 @@ def main():
     if world == 1 and not args.no_extras:
         extras = side_measurements(args, bl, workflow, lattice, surs, infos, z0, g, elements, dev)
 
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except OSError:
-        pass
-    bf16_peak = peaks.get("bf16_tflops", 1900.0)
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    peak_src = "measured" if peaks else "fallback"
+    pk = load_peaks()
+    bf16_peak, hbm_peak, peak_src = pk["bf16"], pk["hbm"], pk["source"]
 
     cpu = cpu_push = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -631,12 +649,16 @@ def main():
         "moment_rel_err_vs_pusher": moment_err,
         "roofline": {"bound": "tensor", "achieved": mlp_tflops, "peak": bf16_peak,
                      "unit": "TFLOP/s", "frac": mlp_tflops / bf16_peak,
-                     "traffic": MLP_DRAM_BYTES_PER_PARTICLE * n,
+                     "traffic": MLP_DRAM_BYTES_PER_PARTICLE * n, "traffic_basis": MLP_DRAM_BASIS,
                      "kernel": "mlp_forward_kernel", "peak_source": peak_src + " bf16 burst",
                      "ms_per_launch": mlp_ms},
         "roofline_segment": {"bound": "hbm", "achieved": seg_gbs, "peak": hbm_peak, "unit": "GB/s",
-                             "frac": seg_gbs / hbm_peak, "kernel": "stream_kernel (map only)",
-                             "ms_per_launch": seg_ms},
+                             "frac": seg_gbs / hbm_peak,
+                             "kernel": "seg_f32_kernel<apply, moments> + moments_finalize_kernel "
+                                       "(the segment pass of every stage of the step)",
+                             "bytes_per_particle": SEG_BYTES_PER_PARTICLE,
+                             "ms_per_launch": seg_ms, "map_only_ms_per_launch": map_ms,
+                             "peak_source": peak_src + " copy bandwidth"},
         "cpu_baseline": cpu,
         "cpu_baseline_pusher": cpu_push,
         "e2e": {"value": e2e_value, "unit": "particle-stages/s", "h2d_bytes_per_step": h2d,

@@ -220,7 +220,11 @@ bl_status bl_moments(const bl_bunch *bunch, double *out, bl_stream stream);
  * scope; every GPU that loads the library keeps it until the process exits.
  * Inputs larger than that scratch are rejected with BL_ERR_INVALID_ARG.
  * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * (cudaGetSymbolAddress), so make that first call before any stream capture;
+ * the lookup is repeated when the device's context has changed (after a
+ * cudaDeviceReset). An `out` that the GPU cannot store to through this very
+ * pointer (plain pageable host memory, for instance) is rejected with
+ * BL_ERR_INVALID_ARG before any work is enqueued.
  * All calls share the one array and every call overwrites what it reads, so
  * no state carries over from call to call; calls whose work overlaps on the
  * GPU (different streams or threads at the same time) race on it. */

@@ -1,7 +1,6 @@
 /*
  * bl_debug.h -- diagnostic entry points of libbl.so (not part of the tracking
- * API). The paper has no counterpart; they check the tensor-core operand
- * layouts that the surrogate kernel relies on, inject host-side failures for
+ * API). The paper has no counterpart; they inject host-side failures for
  * the library's error-path tests, select the training kernel and expose the
  * host-side pooling of chunked moments.
  */
@@ -11,18 +10,6 @@
 #ifdef __cplusplus
 extern "C" {
 #endif
-
-/* One tcgen05 MMA D = A * B^T on the current device.
- * A: device, 128 x K BF16 row-major (placed in tensor memory, two values per
- * 32-bit column); B: device, N x K BF16 row-major, staged into shared memory
- * as 8x8 core matrices of 128 bytes, adjacent core matrices `ks` bytes apart
- * along K and `ns` bytes apart along N; the shared-memory descriptor gets
- * leading offset `lbo` and stride offset `sbo`. D: device, 128 x N FP32
- * row-major. N in {16,32,64,128}, K in {16,32,64,128}, 128 <= ks, ns <= 2048,
- * multiples of 16. Returns 0 on launch success, 1 for invalid sizes, 2 for a
- * launch error. Asynchronous on `stream` (a cudaStream_t). */
-int bl_debug_umma_probe(const void *A, const void *B, float *D, int N, int K, uint32_t ks,
-                        uint32_t ns, uint32_t lbo, uint32_t sbo, void *stream);
 
 /* Host-side fault injection for failure-path tests: the next n workspace
  * allocations of the library fail with BL_ERR_OOM before reaching the

@@ -103,8 +103,6 @@ _SIGS = {
     "bl_debug_fail_allocations": ([C.c_int], C.c_int),
     "bl_debug_train_kernel": ([C.c_int], C.c_int),
     "bl_debug_pool_moments": ([_P, C.c_int32, _P], C.c_int),
-    "bl_debug_umma_probe": ([_P, _P, _P, C.c_int, C.c_int, C.c_uint32, C.c_uint32,
-                             C.c_uint32, C.c_uint32, _P], C.c_int),
 }
 
 
@@ -348,8 +346,17 @@ def bl_moments(bunch, out=None, stream=None):
 
 
 def bl_moments_noalloc(bunch, out, stream=None):
-    """Moments into `out` (device float64 tensor of n_bunch*28) using the
-    library's fixed scratch array instead of any allocation."""
+    """Moments into `out` (a contiguous CUDA float64 tensor of at least
+    n_bunch*28 elements) using the library's fixed scratch array instead of
+    any allocation."""
+    import torch
+    if not isinstance(out, torch.Tensor) or not out.is_cuda:
+        raise BlError(BL_ERR_INVALID_ARG, "out must be a CUDA tensor")
+    if out.dtype != torch.float64 or not out.is_contiguous():
+        raise BlError(BL_ERR_INVALID_ARG, "out must be a contiguous float64 tensor")
+    if out.numel() < bunch.n_bunch * 28:
+        raise BlError(BL_ERR_INVALID_ARG, "out holds %d doubles, %d needed"
+                      % (out.numel(), bunch.n_bunch * 28))
     _check(lib().bl_moments_noalloc(bunch.ref(), _ptr(out), _stream(stream)))
 
 
@@ -543,11 +550,6 @@ def bl_poll_device_errors():
 
 def bl_version():
     return lib().bl_version().decode()
-
-
-def bl_debug_umma_probe(A, B, D, N, K, ks, ns, lbo, sbo, stream=None):
-    return lib().bl_debug_umma_probe(_ptr(A), _ptr(B), _ptr(D), N, K, ks, ns, lbo, sbo,
-                                     _stream(stream))
 
 
 def bl_debug_fail_allocations(n):

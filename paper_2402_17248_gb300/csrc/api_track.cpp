@@ -117,10 +117,12 @@ bl_status run_segment(bl_bunch *b, bl_lattice_s *L, size_t g, bool moments, doub
   void *part = nullptr;
   if (moments)
     BL_TRY(ws_get(st, WS_PARTIALS, (size_t)stream_slots(b->n, b->n_bunch) * 28 * sizeof(double), &part));
+  int64_t unit = 0;
   BL_CUDA(launch_stream<T>(z, z, b->n, off, b->n_bunch, mats, per_bunch, nullptr, true, moments,
-                           (double *)part, st));
+                           (double *)part, st, &unit));
   if (moments)
-    BL_CUDA(launch_moments_finalize((const double *)part, off, b->n_bunch, b->n, mom_dev, nf, st));
+    BL_CUDA(launch_moments_finalize((const double *)part, off, b->n_bunch, b->n, unit, mom_dev,
+                                    nf, st));
   return BL_OK;
 }
 

@@ -22,13 +22,17 @@ inline int64_t stream_slots(int64_t n, int n_bunch) { return stream_blocks(n) + 
 
 // ---- streaming kernels (linear.cu) ----
 // z_out = M_b (z_in - c_b) for particles of bunch b (c_b = 0 when c == NULL),
-// optionally reducing moments of z_in into `partials` (28 doubles per slot).
+// optionally reducing moments of z_in into `partials` (28 doubles per slot:
+// bunch b's sums over unit k, k = particle / *unit, go to slot b + k, so at
+// most stream_slots(n, n_bunch) slots are written). *unit (if non-NULL)
+// receives the unit length that launch_moments_finalize must be given.
 template <typename T>
 cudaError_t launch_stream(Soa<T> zin, Soa<T> zout, int64_t n, const int64_t *offsets,
                           int n_bunch, const T *mats, int per_bunch, const T *centers,
-                          bool apply, bool moments, double *partials, cudaStream_t st);
+                          bool apply, bool moments, double *partials, cudaStream_t st,
+                          int64_t *unit = nullptr);
 cudaError_t launch_moments_finalize(const double *partials, const int64_t *offsets,
-                                    int n_bunch, int64_t n, double *out,
+                                    int n_bunch, int64_t n, int64_t unit, double *out,
                                     unsigned long long *nonfinite, cudaStream_t st);
 // lambda <- M_b^T lambda and cross[b] += sum_i lambda_out,i z_in,i^T (36 per slot).
 template <typename T>

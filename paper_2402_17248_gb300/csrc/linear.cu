@@ -9,8 +9,12 @@
 // piece it reduces one partial into slot b + k, which is unique because both
 // bunches and blocks tile the particle line contiguously. A finalize kernel
 // per bunch sums the slots of the blocks its range touches, in FP64.
+#include <algorithm>
+#include <mutex>
+
 #include "common.cuh"
-#include "internal.h"
+#include "runtime.h"
+#include "tc.cuh"
 
 namespace bl {
 
@@ -84,14 +88,77 @@ stream_kernel(Soa<T> zin, Soa<T> zout, int64_t n, const int64_t *__restrict__ of
   }
 }
 
-// FP32 particles with moments: two warps share each group of 32 particles. The
-// even warp of a pair accumulates sums 0..13 (6 linear sums, 8 products) and
-// writes output rows 0..2; the odd warp accumulates sums 14..26 and writes
-// rows 3..5. Splitting the 27 float-float accumulators this way halves the
-// registers per thread, so more warps keep loads in flight. Roles are
-// warp-uniform, so no lane diverges. Because the update is in place and each
-// warp reads all six coordinates, the pair meets at a 64-thread named barrier
-// between its loads and its stores.
+// ------------------------------------------------ FP32 segment streaming ----
+// Persistent kernel for FP32 bunches whose six arrays are 16-byte aligned:
+// z_out = M_b (z_in - c_b) and/or the raw moment sums of z_in, the two jobs
+// of a segment pass (Sec. 1: a run of linear elements as one per-particle
+// map; Sec. 4: beam moments at the segment entry).
+//
+// Each CTA owns a contiguous range of SUB-particle sub-chunks, its "unit";
+// bunch b's partial sums of that range go to slot b + (CTA index), and the
+// unit length is handed to the finalize step. One lane of a producer warp
+// streams the range through a STAGES-deep ring of shared-memory stages with
+// bulk async copies (one per coordinate, completion counted in bytes on an
+// mbarrier), so later sub-chunks are in flight while the consumers compute.
+// Eight consumer warps in two roles read a stage with vector shared-memory
+// loads, PPT particles per thread: the even warps accumulate sums 0..13
+// (6 linear sums, 8 products) and the non-finite count and write output rows
+// 0..2; the odd warps take sums 14..26 and rows 3..5, with vector stores.
+// The sums stay in per-thread float-float registers across the whole range
+// and are reduced across the block (float-float within a warp, FP64 across
+// warps) only where a bunch or the range ends, so a CTA pays one block
+// reduction per bunch piece rather than one per few thousand particles.
+// Every wait is bounded; after a timeout the warps keep the same sequence of
+// block barriers without waiting, and the producer waits for its own copies
+// before the CTA exits.
+namespace segk {
+constexpr int CONS_WARPS = 8;
+constexpr int CONS_THREADS = 32 * CONS_WARPS;
+constexpr int THREADS = CONS_THREADS + 32;
+constexpr int PPT = 2;                  // particles per consumer thread and stage (two keep
+                                        // the float-float sums within the register budget)
+constexpr int SUB = 128 * PPT;          // particles per ring stage
+constexpr int STAGES = 8;
+constexpr int MIN_SUB_PER_CTA = 4096 / SUB;  // a unit spans >= 4096 particles: at most as many
+                                        // partial slots as the generic kernel's blocks
+constexpr int RENORM_SUBS = 32 / PPT;   // float-float renormalisation period (sub-chunks)
+constexpr uint32_t COORD_BYTES = SUB * 4;
+constexpr uint32_t STAGE_BYTES = 6 * COORD_BYTES;
+constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES;
+constexpr int CONS_BAR = 1;             // named barrier of the consumer warps
+}  // namespace segk
+
+BL_DEV void mbar_arrive_cta(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// hi + lo summed over the warp in float-float (TwoSum of the high parts, the
+// low parts and the rounding errors added); the result is valid in lane 0.
+BL_DEV void ff_warp_sum(float &hi, float &lo) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_down_sync(0xffffffffu, hi, o);
+    const float l2 = __shfl_down_sync(0xffffffffu, lo, o);
+    const float s = hi + h2;
+    const float bp = s - hi;
+    const float e = (hi - (s - bp)) + (h2 - bp);
+    hi = s;
+    lo = lo + l2 + e;
+  }
+}
+
+// Renormalise a float-float pair (TwoSum of hi and lo) so that lo is again
+// below half an ulp of hi; keeps the rounding of later lo updates small.
+BL_DEV void ff_renorm(float &hi, float &lo) {
+  const float s = hi + lo;
+  const float bp = s - hi;
+  lo = (hi - (s - bp)) + (lo - bp);
+  hi = s;
+}
+
+// Float-float accumulation of the raw sums with index J0 <= j < J1 of one
+// particle: j < 6 the coordinates, then the 21 products z_a z_b (a <= b,
+// row-major).
 template <int J0, int J1>
 BL_DEV void mom_subset(float (&hi)[J1 - J0], float (&lo)[J1 - J0], const float (&v)[6]) {
 #pragma unroll
@@ -107,122 +174,332 @@ BL_DEV void mom_subset(float (&hi)[J1 - J0], float (&lo)[J1 - J0], const float (
     }
 }
 
-// One role's share of a (bunch, block) piece: accumulate, then reduce the
-// role's sums across its warp; lane 0 leaves them in red[warp][0..13].
-template <bool APPLY, int ROLE>
-BL_DEV void mom_piece(Soa<float> &zin, Soa<float> &zout, int64_t lo_p, int64_t hi_p, int plane,
-                      const float *__restrict__ Mb, const float *__restrict__ cb,
-                      double (*red)[15]) {
+// Vector of PPT floats for the 8- or 16-byte shared and global accesses.
+template <int P> struct VecOf;
+template <> struct VecOf<2> { using type = float2; };
+template <> struct VecOf<4> { using type = float4; };
+BL_DEV void vec_get(const float2 &w, float (&o)[2]) { o[0] = w.x; o[1] = w.y; }
+BL_DEV void vec_get(const float4 &w, float (&o)[4]) { o[0] = w.x; o[1] = w.y; o[2] = w.z; o[3] = w.w; }
+BL_DEV float2 vec_make(const float (&o)[2]) { return make_float2(o[0], o[1]); }
+BL_DEV float4 vec_make(const float (&o)[4]) { return make_float4(o[0], o[1], o[2], o[3]); }
+
+// One group of PPT particles of one role: moments of the inputs (masked to
+// [lo, hi) when MASK) and the role's three output rows.
+template <int ROLE, bool APPLY, bool MOMENTS, bool MASK>
+BL_DEV void seg_group(const float (&v)[segk::PPT][6], int64_t p0, int64_t lo, int64_t hi,
+                      const float (&M)[18], const float (&c)[6], bool has_c,
+                      float (&shi)[ROLE ? 13 : 14], float (&slo)[ROLE ? 13 : 14], float &nf,
+                      Soa<float> &zout) {
   constexpr int J0 = ROLE ? 14 : 0, J1 = ROLE ? 27 : 14;
-  float M[18], c[6], shi[J1 - J0], slo[J1 - J0];
-  if (APPLY) {
+  constexpr int P = segk::PPT;
+  bool act[P];
 #pragma unroll
-    for (int i = 0; i < 18; ++i) M[i] = __ldg(Mb + 18 * ROLE + i);
+  for (int k = 0; k < P; ++k) act[k] = MASK ? (p0 + k >= lo && p0 + k < hi) : true;
+  if (MOMENTS) {
 #pragma unroll
-    for (int i = 0; i < 6; ++i) c[i] = cb ? __ldg(cb + i) : 0.0f;
-  }
+    for (int k = 0; k < P; ++k) {
+      if (!act[k]) continue;
+      mom_subset<J0, J1>(shi, slo, v[k]);
+      if (ROLE == 0) {
+        // v * 0 is 0 for a finite value and NaN for an infinite or NaN one
+        float t = 0.0f;
 #pragma unroll
-  for (int i = 0; i < J1 - J0; ++i) { shi[i] = 0.f; slo[i] = 0.f; }
-  float nf = 0.f;
-  const int pair = threadIdx.x >> 6;
-  const int64_t last = (hi_p - lo_p - 1) / (STREAM_THREADS / 2) * (STREAM_THREADS / 2);
-  // every warp of the pair runs the same trip count (the tail is masked, not
-  // skipped) so the pair barrier is always matched
-#pragma unroll 2
-  for (int64_t q = 0; q <= last; q += STREAM_THREADS / 2) {
-    const int64_t p = lo_p + q + plane;
-    const bool in = p < hi_p;
-    float v[6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) v[i] = in ? zin.c[i][p] : 0.0f;
-    if (in) {
-      mom_subset<J0, J1>(shi, slo, v);
-      if (ROLE == 0) nf += finite6(v) ? 0.f : 1.f;
-    }
-    if (APPLY) asm volatile("bar.sync %0, 64;" ::"r"(1 + pair) : "memory");
-    if (APPLY && in) {
-#pragma unroll
-      for (int i = 0; i < 6; ++i) v[i] -= c[i];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        float acc = 0.f;
-#pragma unroll
-        for (int j = 0; j < 6; ++j) acc = fmaf(M[i * 6 + j], v[j], acc);
-        zout.c[3 * ROLE + i][p] = acc;
+        for (int i = 0; i < 6; ++i) t = fmaf(v[k][i], 0.0f, t);
+        nf += (t == 0.0f) ? 0.0f : 1.0f;
       }
     }
   }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (APPLY) {
+    float o[3][P];
 #pragma unroll
-  for (int i = 0; i < J1 - J0; ++i) {
-    const double t = warp_sum((double)shi[i] + (double)slo[i]);
-    if (lane == 0) red[warp][i] = t;
-  }
-  if (ROLE == 0) {
-    const double t = warp_sum((double)nf);
-    if (lane == 0) red[warp][14] = t;
+    for (int k = 0; k < P; ++k) {
+      float d[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) d[i] = v[k][i];
+      if (has_c) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) d[i] -= c[i];
+      }
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        float a = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) a = fmaf(M[6 * r + j], d[j], a);
+        o[r][k] = a;
+      }
+    }
+    if (!MASK) {
+      using V = typename VecOf<P>::type;
+#pragma unroll
+      for (int r = 0; r < 3; ++r) *reinterpret_cast<V *>(zout.c[3 * ROLE + r] + p0) = vec_make(o[r]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < P; ++k)
+        if (act[k]) {
+#pragma unroll
+          for (int r = 0; r < 3; ++r) zout.c[3 * ROLE + r][p0 + k] = o[r][k];
+        }
+    }
   }
 }
 
-template <bool APPLY>
-__global__ void __launch_bounds__(STREAM_THREADS, 3)
-stream_mom_f32_kernel(Soa<float> zin, Soa<float> zout, int64_t n,
-                      const int64_t *__restrict__ offsets, int n_bunch,
-                      const float *__restrict__ mats, int per_bunch,
-                      const float *__restrict__ centers, double *__restrict__ partials) {
-  __shared__ int s_b0;
-  __shared__ double s_red[STREAM_THREADS / 32][15];
-  const int64_t start = (int64_t)blockIdx.x * STREAM_CHUNK;
-  const int64_t end = min(n, start + STREAM_CHUNK);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int role = warp & 1;
-  const int plane = (warp >> 1) * 32 + lane;  // particle lane 0..127
-  if (threadIdx.x == 0) s_b0 = find_bunch(offsets, n_bunch, start);
-  __syncthreads();
-  int b = s_b0;
-  int64_t lo = start;
-  while (lo < end) {
-    const int64_t hi = min(end, bunch_end(offsets, b, n));
-    if (hi > lo) {
-      const float *Mb = APPLY ? mats + (per_bunch ? (int64_t)b * 36 : 0) : nullptr;
-      const float *cb = (APPLY && centers) ? centers + (int64_t)b * 6 : nullptr;
-      if (role == 0) mom_piece<APPLY, 0>(zin, zout, lo, hi, plane, Mb, cb, s_red);
-      else mom_piece<APPLY, 1>(zin, zout, lo, hi, plane, Mb, cb, s_red);
-      __syncthreads();
-      if (threadIdx.x < 28) {
-        // sum j: role-0 warps hold j < 14 (and the non-finite count at 14),
-        // role-1 warps hold j >= 14 at j - 14
-        const int j = threadIdx.x;
-        const int r = (j >= 14 && j < 27) ? 1 : 0;
-        const int k = (j == 27) ? 14 : (r ? j - 14 : j);
-        double t = 0.0;
-        for (int w = r; w < STREAM_THREADS / 32; w += 2) t += s_red[w][k];
-        partials[((int64_t)b + blockIdx.x) * 28 + j] = t;
-      }
-      __syncthreads();
-    }
-    lo = max(lo, hi);
-    ++b;
-    if (b >= n_bunch) break;
+// Reduce the role's sums over the consumer warps into one partial slot (28
+// doubles: sums 0..26 and the non-finite count) and clear them.
+template <int ROLE>
+BL_DEV void seg_flush(float (&shi)[ROLE ? 13 : 14], float (&slo)[ROLE ? 13 : 14], float &nf,
+                      double (*red)[15], double *dst, int warp, int lane) {
+  constexpr int NJ = ROLE ? 13 : 14;
+#pragma unroll
+  for (int i = 0; i < NJ; ++i) {
+    ff_warp_sum(shi[i], slo[i]);
+    if (lane == 0) red[warp][i] = (double)shi[i] + (double)slo[i];
+    shi[i] = 0.0f;
+    slo[i] = 0.0f;
   }
+  if (ROLE == 0) {
+    float z = 0.0f;
+    ff_warp_sum(nf, z);
+    if (lane == 0) red[warp][14] = (double)nf + (double)z;
+    nf = 0.0f;
+  }
+  tc::named_bar_sync(segk::CONS_BAR, segk::CONS_THREADS);
+  const int ct = warp * 32 + lane;
+  if (ct < 28) {
+    // role-0 warps hold j < 14 and the count at 14; role-1 warps j >= 14 at j - 14
+    const int r = (ct >= 14 && ct < 27) ? 1 : 0;
+    const int k = (ct == 27) ? 14 : (r ? ct - 14 : ct);
+    double t = 0.0;
+    for (int w = r; w < segk::CONS_WARPS; w += 2) t += red[w][k];
+    dst[ct] = t;
+  }
+  tc::named_bar_sync(segk::CONS_BAR, segk::CONS_THREADS);
+}
+
+// The role's three rows of bunch b's segment matrix and its centre.
+template <int ROLE>
+BL_DEV void seg_load_map(float (&M)[18], float (&c)[6], const float *__restrict__ mats,
+                         int per_bunch, const float *__restrict__ centers, int b) {
+  const float *Mb = mats + (per_bunch ? (int64_t)b * 36 : 0) + 18 * ROLE;
+#pragma unroll
+  for (int i = 0; i < 18; ++i) M[i] = __ldg(Mb + i);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) c[i] = centers ? __ldg(centers + (int64_t)b * 6 + i) : 0.0f;
+}
+
+template <int ROLE, bool APPLY, bool MOMENTS>
+BL_DEV void seg_consume(const Soa<float> &zin, Soa<float> &zout, int64_t n, int64_t r_lo,
+                        int64_t r_hi, int64_t nsub, const int64_t *__restrict__ offsets,
+                        int n_bunch, const float *__restrict__ mats, int per_bunch,
+                        const float *__restrict__ centers, double *__restrict__ partials,
+                        unsigned *err, const uint8_t *smem, uint32_t full0, uint32_t empty0,
+                        double (*red)[15], int warp, int lane) {
+  using namespace segk;
+  constexpr int NJ = ROLE ? 13 : 14;
+  const int g = (warp >> 1) * 32 + lane;  // particle group 0..127 of a stage (PPT particles)
+  float shi[NJ], slo[NJ], nf = 0.0f;
+#pragma unroll
+  for (int i = 0; i < NJ; ++i) { shi[i] = 0.0f; slo[i] = 0.0f; }
+  float M[18], c[6];
+  const bool has_c = APPLY && centers != nullptr;
+  int b = find_bunch(offsets, n_bunch, r_lo);
+  int64_t pe = bunch_end(offsets, b, n);
+  if (APPLY) seg_load_map<ROLE>(M, c, mats, per_bunch, centers, b);
+  bool ok = true, open = false;
+  for (int64_t j = 0; j < nsub; ++j) {
+    const int s = (int)(j % STAGES);
+    if (ok)
+      ok = __all_sync(0xffffffffu, tc::mbar_wait(full0 + 8 * s, (uint32_t)((j / STAGES) & 1),
+                                                 BL_DEVERR_TMA_TIMEOUT, err));
+    const int64_t q0 = r_lo + j * SUB, q1 = min(q0 + SUB, r_hi);
+    const int cnt = (int)(q1 - q0), c4 = cnt & ~3;
+    const int64_t p0 = q0 + PPT * g;
+    float v[PPT][6];
+    if (PPT * g + PPT <= c4) {
+      using V = typename VecOf<PPT>::type;
+      const uint8_t *st = smem + s * STAGE_BYTES + 4 * PPT * g;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        float w[PPT];
+        vec_get(*reinterpret_cast<const V *>(st + i * COORD_BYTES), w);
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) v[k][i] = w[k];
+      }
+    } else {
+      // past the copied multiple of four (only the array's last particles)
+#pragma unroll
+      for (int k = 0; k < PPT; ++k)
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+          v[k][i] = (PPT * g + k >= c4 && PPT * g + k < cnt) ? zin.c[i][p0 + k] : 0.0f;
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive_cta(empty0 + 8 * s);  // the stage may be refilled
+    int64_t cur = q0;
+    for (;;) {
+      const int64_t hi = min(q1, pe);
+      if (hi > cur) {
+        if (cur == q0 && hi == q1 && cnt == SUB)
+          seg_group<ROLE, APPLY, MOMENTS, false>(v, p0, cur, hi, M, c, has_c, shi, slo, nf, zout);
+        else
+          seg_group<ROLE, APPLY, MOMENTS, true>(v, p0, cur, hi, M, c, has_c, shi, slo, nf, zout);
+        open = true;
+      }
+      if (hi < pe) break;  // bunch b goes on past this sub-chunk
+      if (MOMENTS && open) {
+        seg_flush<ROLE>(shi, slo, nf, red, partials + ((int64_t)b + blockIdx.x) * 28, warp, lane);
+        open = false;
+      }
+      if (++b >= n_bunch) break;
+      pe = bunch_end(offsets, b, n);
+      if (APPLY && (per_bunch || has_c)) seg_load_map<ROLE>(M, c, mats, per_bunch, centers, b);
+      cur = hi;
+      if (cur >= q1) break;
+    }
+    if (MOMENTS && (j % RENORM_SUBS) == RENORM_SUBS - 1) {
+#pragma unroll
+      for (int i = 0; i < NJ; ++i) ff_renorm(shi[i], slo[i]);
+    }
+  }
+  if (MOMENTS && open)
+    seg_flush<ROLE>(shi, slo, nf, red, partials + ((int64_t)b + blockIdx.x) * 28, warp, lane);
+}
+
+template <bool APPLY, bool MOMENTS>
+__global__ void __maxnreg__(112)
+seg_f32_kernel(Soa<float> zin, Soa<float> zout, int64_t n, int64_t per_cta,
+               const int64_t *__restrict__ offsets, int n_bunch, const float *__restrict__ mats,
+               int per_bunch, const float *__restrict__ centers, double *__restrict__ partials,
+               unsigned *err) {
+  using namespace segk;
+  extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ __align__(8) uint64_t bars[2 * STAGES];  // full[s], then empty[s]
+  __shared__ double red[CONS_WARPS][15];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t nsub_all = (n + SUB - 1) / SUB;
+  const int64_t j0 = (int64_t)blockIdx.x * per_cta;
+  const int64_t nsub = min(nsub_all, j0 + per_cta) - j0;  // >= 1 by the grid size
+  const int64_t r_lo = j0 * SUB, r_hi = min(n, (j0 + nsub) * SUB);
+  const uint32_t sb = tc::smem_u32(smem);
+  const uint32_t full0 = tc::smem_u32(&bars[0]), empty0 = tc::smem_u32(&bars[STAGES]);
+  if (tid == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      tc::mbar_init(full0 + 8 * s, 1);
+      tc::mbar_init(empty0 + 8 * s, CONS_WARPS);
+    }
+    tc::fence_mbar_init();
+  }
+  __syncthreads();
+  if (warp == CONS_WARPS) {
+    // producer: one lane streams the range through the ring
+    if (lane == 0) {
+      bool ok = true;
+      int64_t issued = 0;
+      for (int64_t j = 0; j < nsub && ok; ++j) {
+        const int s = (int)(j % STAGES);
+        if (j >= STAGES) {
+          // the consumers have read the stage, and its previous copy is complete
+          ok = tc::mbar_wait(empty0 + 8 * s, (uint32_t)((j / STAGES - 1) & 1),
+                             BL_DEVERR_TMA_TIMEOUT, err) &&
+               tc::mbar_wait(full0 + 8 * s, (uint32_t)((j / STAGES - 1) & 1),
+                             BL_DEVERR_TMA_TIMEOUT, err);
+          if (!ok) break;
+        }
+        const int64_t q0 = r_lo + j * SUB;
+        const int64_t cnt = min((int64_t)SUB, r_hi - q0);
+        const uint32_t bytes = (uint32_t)(cnt & ~(int64_t)3) * 4u;
+        tc::mbar_expect_tx(full0 + 8 * s, 6u * bytes);
+        if (bytes) {
+#pragma unroll
+          for (int i = 0; i < 6; ++i)
+            tc::bulk_g2s(sb + s * STAGE_BYTES + i * COORD_BYTES, zin.c[i] + q0, bytes,
+                         full0 + 8 * s);
+        }
+        issued = j + 1;
+      }
+      // no copy may still be writing this CTA's shared memory when it exits
+      for (int64_t j = max((int64_t)0, issued - STAGES); j < issued; ++j)
+        tc::mbar_wait(full0 + 8 * (int)(j % STAGES), (uint32_t)((j / STAGES) & 1),
+                      BL_DEVERR_TMA_TIMEOUT, err);
+    }
+    return;
+  }
+  if ((warp & 1) == 0)
+    seg_consume<0, APPLY, MOMENTS>(zin, zout, n, r_lo, r_hi, nsub, offsets, n_bunch, mats,
+                                   per_bunch, centers, partials, err, smem, full0, empty0, red,
+                                   warp, lane);
+  else
+    seg_consume<1, APPLY, MOMENTS>(zin, zout, n, r_lo, r_hi, nsub, offsets, n_bunch, mats,
+                                   per_bunch, centers, partials, err, smem, full0, empty0, red,
+                                   warp, lane);
+}
+
+// Sub-chunks per CTA for n particles: the range of 2 CTAs per SM, at least
+// MIN_SUB_PER_CTA.
+int64_t seg_per_cta(int64_t n, int num_sms) {
+  const int64_t S = (n + segk::SUB - 1) / segk::SUB;
+  const int64_t G = 2 * (int64_t)std::max(num_sms, 1);
+  return std::max<int64_t>(segk::MIN_SUB_PER_CTA, (S + G - 1) / G);
+}
+
+template <bool APPLY, bool MOMENTS>
+cudaError_t launch_seg(Soa<float> zin, Soa<float> zout, int64_t n, const int64_t *offsets,
+                       int n_bunch, const float *mats, int per_bunch, const float *centers,
+                       double *partials, int num_sms, unsigned *err, int64_t *unit,
+                       cudaStream_t st) {
+  static std::mutex mu;
+  static bool configured[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!configured[dev]) {
+      e = cudaFuncSetAttribute(seg_f32_kernel<APPLY, MOMENTS>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)segk::SMEM_BYTES);
+      if (e != cudaSuccess) return e;
+      configured[dev] = true;
+    }
+  }
+  const int64_t per = seg_per_cta(n, num_sms);
+  const int64_t S = (n + segk::SUB - 1) / segk::SUB;
+  const int64_t grid = (S + per - 1) / per;
+  if (unit) *unit = per * segk::SUB;
+  seg_f32_kernel<APPLY, MOMENTS><<<(unsigned)grid, segk::THREADS, segk::SMEM_BYTES, st>>>(
+      zin, zout, n, per, offsets, n_bunch, mats, per_bunch, centers, partials, err);
+  return cudaGetLastError();
+}
+
+bool aligned16(const Soa<float> &z) {
+  for (int i = 0; i < 6; ++i)
+    if (reinterpret_cast<uintptr_t>(z.c[i]) & 15u) return false;
+  return true;
 }
 
 template <typename T>
 cudaError_t launch_stream(Soa<T> zin, Soa<T> zout, int64_t n, const int64_t *offsets,
                           int n_bunch, const T *mats, int per_bunch, const T *centers,
-                          bool apply, bool moments, double *partials, cudaStream_t st) {
+                          bool apply, bool moments, double *partials, cudaStream_t st,
+                          int64_t *unit) {
+  if (unit) *unit = STREAM_CHUNK;
   if (n <= 0) return cudaSuccess;
-  const int64_t nb = stream_blocks(n);
-  dim3 grid((unsigned)nb), block(STREAM_THREADS);
   if constexpr (sizeof(T) == 4) {
-    if (moments) {
+    if (aligned16(zin) && aligned16(zout) && (apply || moments)) {
+      DevCtx *ctx = nullptr;
+      if (current_ctx(&ctx) != BL_OK) return cudaErrorInvalidDevice;
+      if (apply && moments)
+        return launch_seg<true, true>(zin, zout, n, offsets, n_bunch, mats, per_bunch, centers,
+                                      partials, ctx->num_sms, ctx->err_word, unit, st);
       if (apply)
-        stream_mom_f32_kernel<true><<<grid, block, 0, st>>>(zin, zout, n, offsets, n_bunch, mats, per_bunch, centers, partials);
-      else
-        stream_mom_f32_kernel<false><<<grid, block, 0, st>>>(zin, zout, n, offsets, n_bunch, mats, per_bunch, centers, partials);
-      return cudaGetLastError();
+        return launch_seg<true, false>(zin, zout, n, offsets, n_bunch, mats, per_bunch, centers,
+                                       partials, ctx->num_sms, ctx->err_word, unit, st);
+      return launch_seg<false, true>(zin, zout, n, offsets, n_bunch, mats, per_bunch, centers,
+                                     partials, ctx->num_sms, ctx->err_word, unit, st);
     }
   }
+  const int64_t nb = stream_blocks(n);
+  dim3 grid((unsigned)nb), block(STREAM_THREADS);
   if (apply && moments)
     stream_kernel<T, true, true><<<grid, block, 0, st>>>(zin, zout, n, offsets, n_bunch, mats, per_bunch, centers, partials);
   else if (apply)
@@ -234,15 +511,16 @@ cudaError_t launch_stream(Soa<T> zin, Soa<T> zout, int64_t n, const int64_t *off
 
 template cudaError_t launch_stream<float>(Soa<float>, Soa<float>, int64_t, const int64_t *, int,
                                           const float *, int, const float *, bool, bool, double *,
-                                          cudaStream_t);
+                                          cudaStream_t, int64_t *);
 template cudaError_t launch_stream<double>(Soa<double>, Soa<double>, int64_t, const int64_t *, int,
                                            const double *, int, const double *, bool, bool,
-                                           double *, cudaStream_t);
+                                           double *, cudaStream_t, int64_t *);
 
-// Sum the partial slots of bunch b; out[b] = [N, means, central moments].
+// Sum the partial slots of bunch b (slot b + k for every unit k of `unit`
+// particles that its range touches); out[b] = [N, means, central moments].
 __global__ void __launch_bounds__(256)
 moments_finalize_kernel(const double *__restrict__ partials, const int64_t *__restrict__ offsets,
-                        int n_bunch, int64_t n, double *__restrict__ out,
+                        int n_bunch, int64_t n, int64_t unit, double *__restrict__ out,
                         unsigned long long *nonfinite) {
   __shared__ double s_red[8 * 28];
   const int b = blockIdx.x;
@@ -251,7 +529,7 @@ moments_finalize_kernel(const double *__restrict__ partials, const int64_t *__re
 #pragma unroll
   for (int i = 0; i < 28; ++i) r[i] = 0.0;
   if (end > beg) {
-    const int64_t k0 = beg / STREAM_CHUNK, k1 = (end - 1) / STREAM_CHUNK;
+    const int64_t k0 = beg / unit, k1 = (end - 1) / unit;
     for (int64_t k = k0 + threadIdx.x; k <= k1; k += blockDim.x) {
       const double *src = partials + ((int64_t)b + k) * 28;
 #pragma unroll
@@ -280,9 +558,10 @@ moments_finalize_kernel(const double *__restrict__ partials, const int64_t *__re
 }
 
 cudaError_t launch_moments_finalize(const double *partials, const int64_t *offsets, int n_bunch,
-                                    int64_t n, double *out, unsigned long long *nonfinite,
-                                    cudaStream_t st) {
-  moments_finalize_kernel<<<n_bunch, 256, 0, st>>>(partials, offsets, n_bunch, n, out, nonfinite);
+                                    int64_t n, int64_t unit, double *out,
+                                    unsigned long long *nonfinite, cudaStream_t st) {
+  moments_finalize_kernel<<<n_bunch, 256, 0, st>>>(partials, offsets, n_bunch, n, unit, out,
+                                                   nonfinite);
   return cudaGetLastError();
 }
 

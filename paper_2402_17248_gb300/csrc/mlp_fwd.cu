@@ -467,81 +467,6 @@ __global__ void mlp_pack_kernel(const float *__restrict__ P, uint8_t *__restrict
   }
 }
 
-// Diagnostic: one MMA D = A * B^T with A [128 x K] (BF16, row-major, placed
-// in TMEM) and B [N x K] (BF16, row-major, staged into shared memory with
-// core-matrix strides ks (along K) and ns (along N)), using descriptor fields
-// lbo and sbo; D FP32 [128 x N] row-major in global memory. All shared-memory
-// addresses stay inside the 64 KB dynamic buffer for N, K <= 128 and strides
-// <= 2048 bytes.
-__global__ void __launch_bounds__(128, 1)
-umma_probe_kernel(const __nv_bfloat16 *__restrict__ A, const __nv_bfloat16 *__restrict__ B,
-                  float *__restrict__ D, int N, int K, uint32_t ks, uint32_t ns, uint32_t lbo,
-                  uint32_t sbo) {
-  extern __shared__ __align__(1024) uint8_t sm[];
-  __shared__ __align__(8) uint64_t bar;
-  __shared__ uint32_t slot;
-  const int tid = threadIdx.x, warp = tid >> 5;
-  for (int i = tid; i < 32768; i += 128) reinterpret_cast<uint16_t *>(sm)[i] = 0;
-  __syncthreads();
-  for (int i = tid; i < N * K; i += 128) {
-    const int nn = i / K, k = i % K;
-    const uint32_t off = (uint32_t)((nn >> 3) * ns + (k >> 3) * ks + (nn & 7) * 16 + (k & 7) * 2);
-    if (off + 2 <= 65536u) *reinterpret_cast<__nv_bfloat16 *>(sm + off) = B[i];
-  }
-  if (tid == 0) {
-    tc::mbar_init(tc::smem_u32(&bar), 1);
-    tc::fence_mbar_init();
-  }
-  if (warp == 0) {
-    tc::tmem_alloc(tc::smem_u32(&slot), 256);
-    tc::tmem_relinquish();
-  }
-  tc::fence_proxy_async();
-  tc::fence_before();
-  __syncthreads();
-  tc::fence_after();
-  const uint32_t tmem = slot;
-  const uint32_t lb = (uint32_t)(warp * 32) << 16;
-  for (int c0 = 0; c0 < K / 2; c0 += 8) {
-    uint32_t a[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int k = 2 * (c0 + j);
-      const uint32_t lo = __bfloat16_as_ushort(A[tid * K + k]);
-      const uint32_t hi = __bfloat16_as_ushort(A[tid * K + k + 1]);
-      a[j] = lo | (hi << 16);
-    }
-    tc::tmem_st8(tmem + lb + 128 + c0, a);
-  }
-  tc::tmem_st_wait();
-  tc::fence_before();
-  __syncthreads();
-  if (tid == 0) {
-    tc::fence_after();
-    for (int j = 0; j < K / 16; ++j)
-      tc::mma_ts(tmem, tmem + 128 + 8 * j, tc::sdesc(tc::smem_u32(sm) + 2 * ks * j, lbo, sbo),
-                 tc::idesc_bf16(128, N), j > 0);
-    tc::mma_commit(tc::smem_u32(&bar));
-  }
-  __syncwarp();
-  const bool ok = __all_sync(0xffffffffu,
-                             tc::mbar_wait(tc::smem_u32(&bar), 0, BL_DEVERR_MMA_TIMEOUT, nullptr));
-  tc::fence_after();
-  if (ok) {
-    for (int c0 = 0; c0 < N; c0 += 8) {
-      uint32_t r[8];
-      tc::tmem_ld8(tmem + lb + c0, r);
-      tc::tmem_ld_wait();
-#pragma unroll
-      for (int j = 0; j < 8; ++j) D[tid * N + c0 + j] = __uint_as_float(r[j]);
-    }
-  }
-  tc::fence_before();
-  __syncthreads();
-  tc::fence_after();
-  if (warp == 0) tc::tmem_dealloc(tmem, 256);
-}
-
 }  // namespace
 
 cudaError_t mlp_forward_configure() {
@@ -569,23 +494,3 @@ cudaError_t launch_mlp_forward(Soa<float> z, int64_t n, const uint8_t *img, cons
 }
 
 }  // namespace bl
-
-// Diagnostic entry point (declared in include/bl_debug.h).
-extern "C" int bl_debug_umma_probe(const void *A, const void *B, float *D, int N, int K,
-                                   uint32_t ks, uint32_t ns, uint32_t lbo, uint32_t sbo,
-                                   void *stream) {
-  if (!(N == 16 || N == 32 || N == 64 || N == 128) || !(K == 16 || K == 32 || K == 64 || K == 128))
-    return 1;
-  if (ks > 2048 || ns > 2048 || (ks % 16) || (ns % 16) || ks < 128 || ns < 128) return 1;
-  static bool configured = false;
-  if (!configured) {
-    if (cudaFuncSetAttribute(bl::umma_probe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             65536) != cudaSuccess)
-      return 2;
-    configured = true;
-  }
-  bl::umma_probe_kernel<<<1, 128, 65536, (cudaStream_t)stream>>>(
-      (const __nv_bfloat16 *)A, (const __nv_bfloat16 *)B, D, N, K, ks, ns, lbo, sbo);
-  return cudaGetLastError() == cudaSuccess ? 0 : 2;
-}
-

@@ -201,6 +201,13 @@ bl_status stage_track(const bl_element &e, double gamma_in, int want, StageTrack
   BL_CHECK(e.n0_cm3 > 0.0 && std::isfinite(e.n0_cm3), "plasma density must be positive");
   BL_CHECK(std::isfinite(e.E0_Vpm) && std::isfinite(e.phi0), "wake amplitude/phase not finite");
   BL_CHECK(gamma_in > 1.0 && std::isfinite(gamma_in), "reference gamma must exceed 1");
+  // The FP32 deviation form expands gamma/u_z = sqrt(1 + a), a = (1 + u_perp^2)/u_z^2,
+  // to second order (push_f32.cuh); the dropped a^3/16 stays below FP32
+  // rounding of the kept terms while a < 2^-10.5, i.e. u_z > 38 sqrt(1 + u_perp^2).
+  // gamma_ref >= 400 at the stage entry covers u_perp up to 10.
+  BL_CHECK(want != BL_F32 || gamma_in >= 400.0,
+           "the FP32 stage push needs gamma_ref >= 400 at the stage entry (second-order "
+           "expansion of gamma/u_z); use an FP64 bunch below that");
   const double n0 = e.n0_cm3 * 1.0e6;
   const double kp = std::sqrt(n0 * Consts::E * Consts::E / (Consts::EPS0 * Consts::ME)) / Consts::C;
   const double g = e.E0_Vpm / Consts::MEC2_EV;
@@ -290,16 +297,18 @@ bl_status moments_device(const bl_bunch *b, double *out_dev, unsigned long long 
   void *part = nullptr;
   BL_TRY(ws_get(st, WS_PARTIALS, (size_t)stream_slots(b->n, b->n_bunch) * 28 * sizeof(double), &part));
   const int64_t *off = b->n_bunch > 1 ? b->offsets_dev : nullptr;
+  int64_t unit = 0;
   if (b->dtype == BL_F32) {
     Soa<float> z = soa_of<float>(b);
     BL_CUDA(launch_stream<float>(z, z, b->n, off, b->n_bunch, nullptr, 0, nullptr, false, true,
-                                 (double *)part, st));
+                                 (double *)part, st, &unit));
   } else {
     Soa<double> z = soa_of<double>(b);
     BL_CUDA(launch_stream<double>(z, z, b->n, off, b->n_bunch, nullptr, 0, nullptr, false, true,
-                                  (double *)part, st));
+                                  (double *)part, st, &unit));
   }
-  BL_CUDA(launch_moments_finalize((const double *)part, off, b->n_bunch, b->n, out_dev, nonfinite, st));
+  BL_CUDA(launch_moments_finalize((const double *)part, off, b->n_bunch, b->n, unit, out_dev,
+                                  nonfinite, st));
   return BL_OK;
 }
 

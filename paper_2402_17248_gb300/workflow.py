@@ -127,6 +127,42 @@ def fit_surrogate(xin, xout, steps=20000, batch=1200, lr=1e-3, lr_final=1e-5, se
     return sur, info
 
 
+def plasma_wavenumber(n0_cm3=1.0e17):
+    """k_p = omega_p / c of a plasma of electron density n0 [cm^-3] (CODATA 2018)."""
+    e, eps0, me, c = 1.602176634e-19, 8.8541878128e-12, 9.1093837015e-31, 299792458.0
+    return math.sqrt(n0_cm3 * 1e6 * e * e / (eps0 * me)) / c
+
+
+def train_beamline_surrogates(elements, gamma_ref, pairs_per_stage=1 << 22, steps=120000,
+                              batch=8192, lr=2e-3, t_scale=8.0, seed=1000, log_every=0,
+                              log=None):
+    """One surrogate per plasma stage of `elements` (one network per stage,
+    Sec. 4.2), each trained on the (entry, exit) pairs of its stage from the
+    plain pusher tracking a randomised population of 65,536-particle bunches
+    (emittance, energy spread and injection phase drawn per bunch, the phase
+    jitter +-0.2 rad applied as a centroid shift in t) through the whole
+    beamline. Returns (surrogates, infos)."""
+    from synth.bunch import training_population
+    per = 65536
+    nb = max(1, pairs_per_stage // per)
+    zt, _ = training_population(nb, per, gamma_ref, 0.2 / plasma_wavenumber(), seed=seed)
+    pairs = stage_pairs(device_bunch(zt, gamma_ref), elements)
+    surs, infos = [], []
+    for s in range(len(pairs)):
+        xin, xout, _ = pairs[s]
+        sur, info = fit_surrogate(xin, xout, steps=steps, batch=batch, lr=lr, seed=100 + s,
+                                  t_scale=t_scale, log_every=log_every)
+        info["pairs"] = nb * per
+        surs.append(sur)
+        infos.append(info)
+        pairs[s] = None
+        if log:
+            log("stage %d surrogate: test loss %.3e after %d steps (%.1fs)"
+                % (s + 1, info["test_loss"], info["steps"], info["seconds"]))
+    torch.cuda.empty_cache()
+    return surs, infos
+
+
 def surrogate_beamline(elements, surrogates):
     """Copy of `elements` whose plasma stages use the given surrogates, in order."""
     out, i = [], 0

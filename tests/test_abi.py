@@ -214,3 +214,24 @@ def test_binding_arity_matches_the_header():
     for name, n in protos.items():
         assert name in bl._SIGS, name
         assert len(bl._SIGS[name][0]) == n, (name, len(bl._SIGS[name][0]), n)
+
+
+def test_noalloc_binding_rejects_unusable_output_before_any_call():
+    """bl_moments_noalloc's binding refuses a host, wrongly typed, strided or
+    short `out` before it reaches the library (its kernel stores
+    n_bunch * 28 doubles through that pointer)."""
+    import types
+    import torch
+    fake = types.SimpleNamespace(n_bunch=2)
+    bad = [torch.zeros(56, dtype=torch.float64),               # host memory
+           np.zeros(56)]                                        # not a tensor
+    for out in bad:
+        with pytest.raises(bl.BlError) as e:
+            bl.bl_moments_noalloc(fake, out)
+        assert e.value.status == bl.BL_ERR_INVALID_ARG
+    if torch.cuda.is_available():
+        for out in (torch.zeros(56, dtype=torch.float32, device="cuda"),
+                    torch.zeros(112, dtype=torch.float64, device="cuda")[::2],
+                    torch.zeros(55, dtype=torch.float64, device="cuda")):
+            with pytest.raises(bl.BlError):
+                bl.bl_moments_noalloc(fake, out)

@@ -265,7 +265,8 @@ def test_batched_uneven_bunches_per_bunch_quads():
     mom, nonfin = bl.bl_track(bb, L)
     assert nonfin == 0
     got = from_bunch(bb)
-    worst = 0.0
+    worst = worst_small = 0.0
+    rms0, dpart = None, [[] for _ in range(6)]
     for b in range(len(counts)):
         sl = slice(off[b], off[b + 1])
         zb = [c[sl] for c in z]
@@ -285,11 +286,34 @@ def test_batched_uneven_bunches_per_bunch_quads():
                 S = moments.sigma_matrix(want)
                 sd = np.sqrt(np.diag(S))
                 for j, (p, q) in enumerate(moments.PAIRS):
-                    worst = max(worst, abs(m[7 + j] - want[7 + j]) / (sd[p] * sd[q]))
-    print("batched: worst second-moment difference / (sd_a sd_b) vs oracle: %.3e" % worst)
+                    d = abs(m[7 + j] - want[7 + j]) / (sd[p] * sd[q])
+                    if counts[b] > 1000:
+                        worst = max(worst, d)
+                    else:
+                        worst_small = max(worst_small, d)
+        # and the particles themselves, one by one (scaled by the rms of the
+        # largest bunch's output, which tiny bunches do not have of their own)
+        if counts[b]:
+            if rms0 is None:
+                rms0 = [np.std(c) for c in zo]
+            for c in range(6):
+                d = np.abs(got[c][sl] - zo[c])
+                dpart[c].append(d / rms0[c])
+                assert np.all(d <= 2e-3 * rms0[c] + 2.0 ** -6 * np.abs(zo[c]))
+    dall = [np.concatenate(v) for v in dpart]
+    worst_particle = max(float(np.median(v)) for v in dall)
+    within = min(float(np.mean(v <= 2e-3)) for v in dall)
+    print("batched vs oracle: worst second-moment difference / (sd_a sd_b) %.3e (bunches "
+          "> 1000 particles), %.3e (smaller); particles: worst median difference / rms %.3e, "
+          "fraction within 2e-3 rms %.5f" % (worst, worst_small, worst_particle, within))
+    assert within >= 0.99
     # downstream stages quantise their inputs to BF16; particles whose FP32
-    # input lies within rounding of a BF16 midpoint move by one BF16 ulp
-    assert worst < 2e-3
+    # input lies within rounding of a BF16 midpoint move by one BF16 ulp, so
+    # a bunch of a few particles can move by a sizeable part of its spread
+    # (measured 2e-5 on the large bunches)
+    assert worst < 2e-4
+    assert worst_small < 2e-3
+    assert worst_particle < 1e-4
 
 
 def test_trained_surrogate_gain_over_pusher():
@@ -328,7 +352,11 @@ def test_trained_surrogate_gain_over_pusher():
     print("speedup %.1fx; relative moment differences %s" % (tp / ts, err))
     assert tp / ts > 5
     assert info["test_loss"] < 0.05
-    assert err["rel_energy_spread"] < 0.05
+    # measured 6e-3 (emittances) and 4e-4 (energy spread) after this short
+    # fit; the 8-stage beamline at the benchmark's training length is held
+    # to 2e-3 in test_gpu_learned.py
+    assert err["eps_n_x"] < 2e-2 and err["eps_n_y"] < 2e-2
+    assert err["rel_energy_spread"] < 2e-3
 
 
 @pytest.mark.parametrize("width", [3.5, 2.0, 0.7])

@@ -146,12 +146,14 @@ def test_gradient_matches_oracle(train_kernel, batch):
     print("%s batch %d: loss gpu %.6e oracle %.6e; gradient normwise rel err %.3e"
           % (train_kernel, batch, loss.item(), L, rel))
     assert abs(loss.item() / L - 1) < 1e-3
-    assert rel < 1e-2
+    # tanh.approx (relative error 2^-11) in the forward's GELU is the
+    # largest term; measured 1e-5 .. 2e-4
+    assert rel < 1e-3
     # per layer: every block of the flat vector is filled, not only the large ones
     offs = [0, 768, 896, 17280, 17408, 33792, 33920, 50304, 50432, 51200, 51206]
     for a, b in zip(offs[:-1], offs[1:]):
         ra = np.linalg.norm(g[a:b] - flat[a:b]) / np.linalg.norm(flat[a:b])
-        assert ra < 3e-2, (a, b, ra)
+        assert ra < 5e-3, (a, b, ra)
 
 
 def test_gradient_kernels_agree():
@@ -260,3 +262,65 @@ def test_surrogate_file_round_trip_and_resume(tmp_path):
     torch.cuda.synchronize()
     for x, y in zip(a.params(), b.params()):
         assert all(np.array_equal(u, v) for u, v in zip(x, y))
+
+
+def _read_surrogate_file(path):
+    """FP32 masters, Adam m and v and the step count of a surrogate file
+    (layout of bl_surrogate_save: magic, version, widths, FP64 normalisation,
+    domain flag and box, step, then the three flat FP32 vectors)."""
+    raw = open(path, "rb").read()
+    off = 8 + 4 + 6 * 4 + 4 * 6 * 8 + 4 + 2 * 6 * 4
+    step = int(np.frombuffer(raw, dtype=np.int32, count=1, offset=off)[0])
+    off += 4
+    n = 51206
+    P = np.frombuffer(raw, dtype=np.float32, count=n, offset=off)
+    M = np.frombuffer(raw, dtype=np.float32, count=n, offset=off + 4 * n)
+    V = np.frombuffer(raw, dtype=np.float32, count=n, offset=off + 8 * n)
+    return step, P.astype(np.float64), M.astype(np.float64), V.astype(np.float64)
+
+
+def test_adam_over_many_steps_matches_oracle(tmp_path):
+    """50 Adam steps of bl_surrogate_train_step on fixed index batches: the
+    FP32 masters and the first and second moments m, v read back from the
+    surrogate file agree with the oracle's FP64 Adam (bias-corrected,
+    Kingma and Ba Alg. 1) fed the same minibatch gradients, so the m and v
+    recurrences and the bias corrections for t > 1 are checked, not only
+    the first step."""
+    import torch
+    from paper_2402_17248_gb300 import bl
+    Zi, Zo = _pairs(20000, 17)
+    mu_i, sd_i = Zi.mean(axis=1), Zi.std(axis=1)
+    mu_o, sd_o = Zo.mean(axis=1), Zo.std(axis=1)
+    Ws, bs = mlp_init(WIDTHS, 5)
+    sur = bl.Surrogate(Ws, bs, mu_i, sd_i, mu_o, sd_o)
+    din = torch.tensor(Zi, device="cuda")
+    dout = torch.tensor(Zo, device="cuda")
+    rng = np.random.default_rng(6)
+    steps, batch, lr, b1, b2, eps = 50, 1024, 2e-3, 0.9, 0.999, 1e-8
+    path = str(tmp_path / "s.blsur")
+    sur.save(path)
+    t0, p0, m0, v0 = _read_surrogate_file(path)
+    assert t0 == 0 and not m0.any() and not v0.any()
+    grads = []
+    g = torch.zeros(bl.BL_MLP_NPARAM, device="cuda")
+    for t in range(steps):
+        idx = torch.tensor(rng.permutation(20000)[:batch], device="cuda", dtype=torch.int64)
+        bl.bl_surrogate_grad(sur, din, dout, g, idx=idx)
+        grads.append(g.cpu().numpy().astype(np.float64))
+        bl.bl_surrogate_train_step(sur, din, dout, idx=idx, lr=lr, beta1=b1, beta2=b2, eps=eps)
+    torch.cuda.synchronize()
+    sur.save(path)
+    t1, p1, m1, v1 = _read_surrogate_file(path)
+    assert t1 == steps
+    opt = mlp.Adam([p0], lr=lr, b1=b1, b2=b2, eps=eps)
+    p = [p0]
+    for gr in grads:
+        p = opt.step(p, [gr])
+    rm = np.linalg.norm(m1 - opt.m[0]) / np.linalg.norm(opt.m[0])
+    rv = np.linalg.norm(v1 - opt.v[0]) / np.linalg.norm(opt.v[0])
+    disp = p[0] - p0
+    rp = np.linalg.norm((p1 - p0) - disp) / np.linalg.norm(disp)
+    print("after %d Adam steps: m %.2e, v %.2e, displacement of the masters %.2e (normwise rel)"
+          % (steps, rm, rv, rp))
+    assert rm < 1e-6 and rv < 1e-6
+    assert rp < 1e-5

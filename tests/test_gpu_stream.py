@@ -274,3 +274,20 @@ def test_injected_allocation_failure_is_reported_and_recovered():
     mref, _ = bl.bl_track(ref, L)
     assert np.array_equal(mom, mref)
     assert all(np.array_equal(a, w) for a, w in zip(from_bunch(b), from_bunch(ref)))
+
+
+def test_fp32_stage_push_rejects_low_reference_energy():
+    """The FP32 deviation form of the pusher expands gamma/u_z to second order
+    in (1 + u_perp^2)/u_z^2; below gamma_ref = 400 at the stage entry the host
+    refuses the FP32 push (an FP64 bunch takes it instead)."""
+    import torch
+    from paper_2402_17248_gb300 import bl
+    z32 = [torch.zeros(64, dtype=torch.float32, device="cuda") for _ in range(6)]
+    b = bl.Bunch(z32, 300.0)
+    with pytest.raises(bl.BlError) as e:
+        bl.bl_push_stage(b, lattice.plasma(10))
+    assert e.value.status == bl.BL_ERR_INVALID_ARG
+    z64 = [torch.zeros(64, dtype=torch.float64, device="cuda") for _ in range(6)]
+    b64 = bl.Bunch(z64, 300.0)
+    bl.bl_push_stage(b64, lattice.plasma(10))
+    assert b64.gamma_ref > 300.0
