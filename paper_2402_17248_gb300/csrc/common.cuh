@@ -15,22 +15,25 @@ enum : unsigned { BL_DEVERR_MMA_TIMEOUT = 1u, BL_DEVERR_TMA_TIMEOUT = 2u, BL_DEV
 // of lo, and TwoProd (an fma residual) makes each product of two FP32 values
 // exact. The relative error of a float-float accumulation is about 2^-44,
 // enough for FP64-quality second moments without per-particle FP64 work.
+// The additions and the product are written with the _rn intrinsics, which
+// the compiler never contracts into an fma: a contracted hi + a*b would
+// round the exact product away and break the error-free transformations.
 BL_DEV void ff_add(float &hi, float &lo, float p) {
-  float s = hi + p;
-  float bp = s - hi;
-  float err = (hi - (s - bp)) + (p - bp);
+  const float s = __fadd_rn(hi, p);
+  const float bp = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));
   hi = s;
-  lo += err;
+  lo = __fadd_rn(lo, err);
 }
 
 BL_DEV void ff_add_prod(float &hi, float &lo, float a, float b) {
-  float p = a * b;
-  float e = fmaf(a, b, -p);
-  float s = hi + p;
-  float bp = s - hi;
-  float err = (hi - (s - bp)) + (p - bp);
+  const float p = __fmul_rn(a, b);
+  const float e = fmaf(a, b, -p);
+  const float s = __fadd_rn(hi, p);
+  const float bp = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));
   hi = s;
-  lo += err + e;
+  lo = __fadd_rn(lo, __fadd_rn(err, e));
 }
 
 // Raw moment sums of one particle: 6 coordinates and their 21 products

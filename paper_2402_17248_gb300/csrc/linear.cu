@@ -96,27 +96,27 @@ stream_kernel(Soa<T> zin, Soa<T> zout, int64_t n, const int64_t *__restrict__ of
 //
 // Each CTA owns a contiguous range of SUB-particle sub-chunks, its "unit";
 // bunch b's partial sums of that range go to slot b + (CTA index), and the
-// unit length is handed to the finalize step. One lane of a producer warp
-// streams the range through a STAGES-deep ring of shared-memory stages with
-// bulk async copies (one per coordinate, completion counted in bytes on an
-// mbarrier), so later sub-chunks are in flight while the consumers compute.
-// Eight consumer warps in two roles read a stage with vector shared-memory
-// loads, PPT particles per thread: the even warps accumulate sums 0..13
-// (6 linear sums, 8 products) and the non-finite count and write output rows
-// 0..2; the odd warps take sums 14..26 and rows 3..5, with vector stores.
-// The sums stay in per-thread float-float registers across the whole range
-// and are reduced across the block (float-float within a warp, FP64 across
-// warps) only where a bunch or the range ends, so a CTA pays one block
-// reduction per bunch piece rather than one per few thousand particles.
-// Every wait is bounded; after a timeout the warps keep the same sequence of
-// block barriers without waiting, and the producer waits for its own copies
-// before the CTA exits.
+// unit length is handed to the finalize step. The range streams through a
+// STAGES-deep ring of shared-memory stages filled by bulk async copies (one
+// per coordinate, completion counted in bytes on an mbarrier): the first
+// STAGES are issued at the start, and each later one by the last warp to
+// release the stage it reuses, so later sub-chunks are in flight while the
+// warps compute and no warp is set aside for the copies. Eight warps in two
+// roles read a stage with vector shared-memory loads, PPT particles per
+// thread: the even warps accumulate sums 0..13 (6 linear sums, 8 products)
+// and the non-finite count and write output rows 0..2; the odd warps take
+// sums 14..26 and rows 3..5, with vector stores. The sums stay in per-thread
+// float-float registers across the whole range and are reduced across the
+// block (float-float within a warp, FP64 across warps) only where a bunch or
+// the range ends, so a CTA pays one block reduction per bunch piece rather
+// than one per few thousand particles. Every wait is bounded; after a
+// timeout the warps keep the same sequence of block barriers without
+// waiting, and the CTA waits for its own copies before it exits.
 namespace segk {
-constexpr int CONS_WARPS = 8;
-constexpr int CONS_THREADS = 32 * CONS_WARPS;
-constexpr int THREADS = CONS_THREADS + 32;
-constexpr int PPT = 2;                  // particles per consumer thread and stage (two keep
-                                        // the float-float sums within the register budget)
+constexpr int WARPS = 8;
+constexpr int THREADS = 32 * WARPS;
+constexpr int PPT = 2;                  // particles per thread and stage (two keep the
+                                        // float-float sums within the register budget)
 constexpr int SUB = 128 * PPT;          // particles per ring stage
 constexpr int STAGES = 8;
 constexpr int MIN_SUB_PER_CTA = 4096 / SUB;  // a unit spans >= 4096 particles: at most as many
@@ -125,7 +125,6 @@ constexpr int RENORM_SUBS = 32 / PPT;   // float-float renormalisation period (s
 constexpr uint32_t COORD_BYTES = SUB * 4;
 constexpr uint32_t STAGE_BYTES = 6 * COORD_BYTES;
 constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES;
-constexpr int CONS_BAR = 1;             // named barrier of the consumer warps
 }  // namespace segk
 
 BL_DEV void mbar_arrive_cta(uint32_t bar) {
@@ -139,21 +138,36 @@ BL_DEV void ff_warp_sum(float &hi, float &lo) {
   for (int o = 16; o > 0; o >>= 1) {
     const float h2 = __shfl_down_sync(0xffffffffu, hi, o);
     const float l2 = __shfl_down_sync(0xffffffffu, lo, o);
-    const float s = hi + h2;
-    const float bp = s - hi;
-    const float e = (hi - (s - bp)) + (h2 - bp);
+    const float s = __fadd_rn(hi, h2);
+    const float bp = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(h2, bp));
     hi = s;
-    lo = lo + l2 + e;
+    lo = __fadd_rn(__fadd_rn(lo, l2), e);
   }
 }
 
 // Renormalise a float-float pair (TwoSum of hi and lo) so that lo is again
 // below half an ulp of hi; keeps the rounding of later lo updates small.
 BL_DEV void ff_renorm(float &hi, float &lo) {
-  const float s = hi + lo;
-  const float bp = s - hi;
-  lo = (hi - (s - bp)) + (lo - bp);
+  const float s = __fadd_rn(hi, lo);
+  const float bp = __fsub_rn(s, hi);
+  lo = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(lo, bp));
   hi = s;
+}
+
+// Issue the bulk copies of sub-chunk j (particles [q0, q0 + cnt)) into ring
+// stage s: the largest multiple of four particles of each coordinate (16-byte
+// sizes); the rest are read from global memory by the threads.
+BL_DEV void seg_issue(const Soa<float> &zin, int64_t q0, int64_t cnt, int s, uint32_t sb,
+                      uint32_t full) {
+  const uint32_t bytes = (uint32_t)(cnt & ~(int64_t)3) * 4u;
+  tc::mbar_expect_tx(full, 6u * bytes);
+  if (bytes) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+      tc::bulk_g2s(sb + s * segk::STAGE_BYTES + i * segk::COORD_BYTES, zin.c[i] + q0, bytes,
+                   full);
+  }
 }
 
 // Float-float accumulation of the raw sums with index J0 <= j < J1 of one
@@ -243,7 +257,7 @@ BL_DEV void seg_group(const float (&v)[segk::PPT][6], int64_t p0, int64_t lo, in
   }
 }
 
-// Reduce the role's sums over the consumer warps into one partial slot (28
+// Reduce the role's sums over the block's warps into one partial slot (28
 // doubles: sums 0..26 and the non-finite count) and clear them.
 template <int ROLE>
 BL_DEV void seg_flush(float (&shi)[ROLE ? 13 : 14], float (&slo)[ROLE ? 13 : 14], float &nf,
@@ -262,17 +276,17 @@ BL_DEV void seg_flush(float (&shi)[ROLE ? 13 : 14], float (&slo)[ROLE ? 13 : 14]
     if (lane == 0) red[warp][14] = (double)nf + (double)z;
     nf = 0.0f;
   }
-  tc::named_bar_sync(segk::CONS_BAR, segk::CONS_THREADS);
+  __syncthreads();
   const int ct = warp * 32 + lane;
   if (ct < 28) {
     // role-0 warps hold j < 14 and the count at 14; role-1 warps j >= 14 at j - 14
     const int r = (ct >= 14 && ct < 27) ? 1 : 0;
     const int k = (ct == 27) ? 14 : (r ? ct - 14 : ct);
     double t = 0.0;
-    for (int w = r; w < segk::CONS_WARPS; w += 2) t += red[w][k];
+    for (int w = r; w < segk::WARPS; w += 2) t += red[w][k];
     dst[ct] = t;
   }
-  tc::named_bar_sync(segk::CONS_BAR, segk::CONS_THREADS);
+  __syncthreads();
 }
 
 // The role's three rows of bunch b's segment matrix and its centre.
@@ -291,8 +305,9 @@ BL_DEV void seg_consume(const Soa<float> &zin, Soa<float> &zout, int64_t n, int6
                         int64_t r_hi, int64_t nsub, const int64_t *__restrict__ offsets,
                         int n_bunch, const float *__restrict__ mats, int per_bunch,
                         const float *__restrict__ centers, double *__restrict__ partials,
-                        unsigned *err, const uint8_t *smem, uint32_t full0, uint32_t empty0,
-                        double (*red)[15], int warp, int lane) {
+                        unsigned *err, const uint8_t *smem, uint32_t sb, uint32_t full0,
+                        uint32_t empty0, int *s_cnt, long long *s_issued, double (*red)[15],
+                        int warp, int lane) {
   using namespace segk;
   constexpr int NJ = ROLE ? 13 : 14;
   const int g = (warp >> 1) * 32 + lane;  // particle group 0..127 of a stage (PPT particles)
@@ -332,8 +347,26 @@ BL_DEV void seg_consume(const Soa<float> &zin, Soa<float> &zout, int64_t n, int6
         for (int i = 0; i < 6; ++i)
           v[k][i] = (PPT * g + k >= c4 && PPT * g + k < cnt) ? zin.c[i][p0 + k] : 0.0f;
     }
+    // release the stage; the last warp to do so refills it with sub-chunk
+    // j + STAGES once every warp's arrival has completed the empty phase
     __syncwarp();
-    if (lane == 0) mbar_arrive_cta(empty0 + 8 * s);  // the stage may be refilled
+    if (lane == 0) {
+      mbar_arrive_cta(empty0 + 8 * s);
+      if (atomicAdd(&s_cnt[s], 1) == WARPS - 1) {
+        s_cnt[s] = 0;
+        const int64_t jn = j + STAGES;
+        if (jn < nsub &&
+            tc::mbar_wait(empty0 + 8 * s, (uint32_t)((j / STAGES) & 1), BL_DEVERR_TMA_TIMEOUT,
+                          err)) {
+          const int64_t qn = r_lo + jn * SUB;
+          seg_issue(zin, qn, min((int64_t)SUB, r_hi - qn), s, sb, full0 + 8 * s);
+          *s_issued = jn + 1;
+        }
+      }
+    }
+    // in place, the particles past the copied part are read from global
+    // memory: every warp reads them before any warp stores (last sub-chunk)
+    if (c4 < cnt) __syncthreads();
     int64_t cur = q0;
     for (;;) {
       const int64_t hi = min(q1, pe);
@@ -365,7 +398,7 @@ BL_DEV void seg_consume(const Soa<float> &zin, Soa<float> &zout, int64_t n, int6
 }
 
 template <bool APPLY, bool MOMENTS>
-__global__ void __maxnreg__(112)
+__global__ void __launch_bounds__(segk::THREADS, 2)
 seg_f32_kernel(Soa<float> zin, Soa<float> zout, int64_t n, int64_t per_cta,
                const int64_t *__restrict__ offsets, int n_bunch, const float *__restrict__ mats,
                int per_bunch, const float *__restrict__ centers, double *__restrict__ partials,
@@ -373,7 +406,9 @@ seg_f32_kernel(Soa<float> zin, Soa<float> zout, int64_t n, int64_t per_cta,
   using namespace segk;
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ __align__(8) uint64_t bars[2 * STAGES];  // full[s], then empty[s]
-  __shared__ double red[CONS_WARPS][15];
+  __shared__ double red[WARPS][15];
+  __shared__ int s_cnt[STAGES];       // warps that have released stage s in its current round
+  __shared__ long long s_issued;      // sub-chunks whose copies have been issued
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t nsub_all = (n + SUB - 1) / SUB;
   const int64_t j0 = (int64_t)blockIdx.x * per_cta;
@@ -384,53 +419,35 @@ seg_f32_kernel(Soa<float> zin, Soa<float> zout, int64_t n, int64_t per_cta,
   if (tid == 0) {
     for (int s = 0; s < STAGES; ++s) {
       tc::mbar_init(full0 + 8 * s, 1);
-      tc::mbar_init(empty0 + 8 * s, CONS_WARPS);
+      tc::mbar_init(empty0 + 8 * s, WARPS);
+      s_cnt[s] = 0;
     }
     tc::fence_mbar_init();
+    const int64_t first = min((int64_t)STAGES, nsub);
+    for (int64_t j = 0; j < first; ++j) {
+      const int64_t q0 = r_lo + j * SUB;
+      seg_issue(zin, q0, min((int64_t)SUB, r_hi - q0), (int)j, sb, full0 + 8 * (int)j);
+    }
+    s_issued = first;
   }
   __syncthreads();
-  if (warp == CONS_WARPS) {
-    // producer: one lane streams the range through the ring
-    if (lane == 0) {
-      bool ok = true;
-      int64_t issued = 0;
-      for (int64_t j = 0; j < nsub && ok; ++j) {
-        const int s = (int)(j % STAGES);
-        if (j >= STAGES) {
-          // the consumers have read the stage, and its previous copy is complete
-          ok = tc::mbar_wait(empty0 + 8 * s, (uint32_t)((j / STAGES - 1) & 1),
-                             BL_DEVERR_TMA_TIMEOUT, err) &&
-               tc::mbar_wait(full0 + 8 * s, (uint32_t)((j / STAGES - 1) & 1),
-                             BL_DEVERR_TMA_TIMEOUT, err);
-          if (!ok) break;
-        }
-        const int64_t q0 = r_lo + j * SUB;
-        const int64_t cnt = min((int64_t)SUB, r_hi - q0);
-        const uint32_t bytes = (uint32_t)(cnt & ~(int64_t)3) * 4u;
-        tc::mbar_expect_tx(full0 + 8 * s, 6u * bytes);
-        if (bytes) {
-#pragma unroll
-          for (int i = 0; i < 6; ++i)
-            tc::bulk_g2s(sb + s * STAGE_BYTES + i * COORD_BYTES, zin.c[i] + q0, bytes,
-                         full0 + 8 * s);
-        }
-        issued = j + 1;
-      }
-      // no copy may still be writing this CTA's shared memory when it exits
-      for (int64_t j = max((int64_t)0, issued - STAGES); j < issued; ++j)
-        tc::mbar_wait(full0 + 8 * (int)(j % STAGES), (uint32_t)((j / STAGES) & 1),
-                      BL_DEVERR_TMA_TIMEOUT, err);
-    }
-    return;
-  }
   if ((warp & 1) == 0)
     seg_consume<0, APPLY, MOMENTS>(zin, zout, n, r_lo, r_hi, nsub, offsets, n_bunch, mats,
-                                   per_bunch, centers, partials, err, smem, full0, empty0, red,
-                                   warp, lane);
+                                   per_bunch, centers, partials, err, smem, sb, full0, empty0,
+                                   s_cnt, &s_issued, red, warp, lane);
   else
     seg_consume<1, APPLY, MOMENTS>(zin, zout, n, r_lo, r_hi, nsub, offsets, n_bunch, mats,
-                                   per_bunch, centers, partials, err, smem, full0, empty0, red,
-                                   warp, lane);
+                                   per_bunch, centers, partials, err, smem, sb, full0, empty0,
+                                   s_cnt, &s_issued, red, warp, lane);
+  // no copy may still be writing this CTA's shared memory when it exits (the
+  // warps have waited for every copy, unless a wait timed out)
+  __syncthreads();
+  if (tid == 0) {
+    const long long issued = s_issued;
+    for (long long j = max(0ll, issued - STAGES); j < issued; ++j)
+      tc::mbar_wait(full0 + 8 * (int)(j % STAGES), (uint32_t)((j / STAGES) & 1),
+                    BL_DEVERR_TMA_TIMEOUT, err);
+  }
 }
 
 // Sub-chunks per CTA for n particles: the range of 2 CTAs per SM, at least

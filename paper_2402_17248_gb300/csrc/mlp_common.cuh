@@ -30,30 +30,32 @@ __host__ __device__ inline uint32_t img_off(int n, int k, int K) {
   return (uint32_t)((n >> 3) * (K / 8) * 128 + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2);
 }
 
-// Double-float helpers: a value v is carried as hi + lo (FP32 each).
+// Double-float helpers: a value v is carried as hi + lo (FP32 each). The
+// additions and products that must round exactly once are written with the
+// _rn intrinsics, which are never contracted into an fma.
 BL_DEV void two_sum(float a, float b, float &s, float &e) {
-  s = a + b;
-  const float bp = s - a;
-  e = (a - (s - bp)) + (b - bp);
+  s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
 }
 
 // (z - mu) * inv with mu = mh + ml and inv = ih + il, rounded to FP32.
 BL_DEV float df_normalise(float z, float mh, float ml, float ih, float il) {
   float dh, dl;
   two_sum(z, -mh, dh, dl);
-  dl -= ml;
-  const float p = dh * ih;
+  dl = __fsub_rn(dl, ml);
+  const float p = __fmul_rn(dh, ih);
   const float pe = fmaf(dh, ih, -p);
-  return p + (pe + fmaf(dh, il, dl * ih));
+  return __fadd_rn(p, __fadd_rn(pe, fmaf(dh, il, __fmul_rn(dl, ih))));
 }
 
 // y * sd + mu with sd = sh + sl and mu = mh + ml, rounded to FP32.
 BL_DEV float df_affine(float y, float sh, float sl, float mh, float ml) {
-  const float p = y * sh;
+  const float p = __fmul_rn(y, sh);
   const float pe = fmaf(y, sh, -p);
   float s, se;
   two_sum(p, mh, s, se);
-  return s + (se + pe + fmaf(y, sl, ml));
+  return __fadd_rn(s, __fadd_rn(__fadd_rn(se, pe), fmaf(y, sl, ml)));
 }
 
 BL_DEV void mbar_arrive(uint32_t bar) {

@@ -3,29 +3,30 @@
 // every particle in place (Sec. 4.3: in-situ inference on device-resident
 // particles, with the normalise / de-normalise data preparation fused).
 //
-// Design (one persistent CTA per SM, three 128-particle tile slots per CTA,
-// warp-specialised: 24 epilogue warps, an MMA-issuing warp, a fallback warp):
+// Design (one persistent CTA per SM, two 128-particle tile slots per CTA,
+// warp-specialised: 16 epilogue warps, an MMA-issuing warp, a fallback warp):
 //  * The weight matrices and bias blocks (BF16, ~117 KB) are copied once per
 //    CTA into shared memory by bulk async copies and stay there for all
 //    tiles. They are the B operand of every MMA, in the K-major no-swizzle
 //    core-matrix layout prepared by the pack kernel.
-//  * A tile's activations never leave the SM. Each layer's accumulator
-//    D[128 particles x N] (FP32) is in tensor memory, 128 columns per slot;
-//    the slot's epilogue warpgroup reads it (tcgen05.ld), applies GELU,
-//    rounds to BF16 and writes the row into the slot's 32 KB activation
-//    buffer in shared memory, in the same K-major core-matrix layout as the
-//    weights: the A operand of the next layer's MMA. Keeping activations out
-//    of tensor memory leaves room for three tiles in flight, so the MMAs of
-//    one tile and the tanh work of the two others overlap.
+//  * A tile's activations never leave tensor memory. Each layer's
+//    accumulator D[128 particles x N] (FP32) takes 128 columns of the slot;
+//    the slot's epilogue warpgroups read it (tcgen05.ld), apply GELU, round
+//    to BF16 and write the row back into the slot's 64-column activation
+//    region (tcgen05.st, two BF16 per column): the A operand of the next
+//    layer's MMA, read by the tensor core from tensor memory. With both
+//    operands in shared memory an N = 128 MMA would read all 128 bytes per
+//    clock the SM's shared memory delivers, and the epilogue's stores would
+//    wait for every MMA in flight; with A in tensor memory the MMAs read only
+//    the weights from shared memory and the epilogue touches no shared
+//    memory, so the MMAs of one tile and the tanh work of the other overlap.
 //  * One lane of the MMA warp issues every MMA with descriptors precomputed
-//    once, so a K step costs one 64-bit add; every hidden-layer
-//    MMA is M=128 x N=128 (x K=16), which the tensor core runs at its full
-//    rate even as a dependent accumulation chain with both operands in
-//    shared memory. The MMA warp and the warpgroups hand buffers to each
-//    other through mbarriers (MMA-complete: commit-arrived; epilogue-complete:
-//    128 thread arrivals).
+//    once, so a K step costs one add; every hidden-layer MMA is M=128 x
+//    N=128 (x K=16). The MMA warp and the warpgroups hand the tensor-memory
+//    regions to each other through mbarriers (MMA-complete: commit-arrived;
+//    epilogue-complete: 256 thread arrivals).
 //  * Biases ride in the MMA: one extra K=16 step multiplies a constant
-//    shared-memory A matrix whose first two K columns are 1 by the bias split
+//    tensor-memory A matrix whose first two K columns are 1 by the bias split
 //    into BF16 hi and lo parts.
 //  * GELU: u = x (c0 + c1 x^2) in packed FP32x2, tanh.approx.f32, and
 //    2*GELU = x (1 + tanh u) as an FP32x2 FMA, rounded once to BF16. Hidden
@@ -50,7 +51,7 @@ namespace {
 
 using namespace mlp;
 
-constexpr int SLOTS = 3;
+constexpr int SLOTS = 2;
 constexpr int WG_PER_SLOT = 2;                     // epilogue warpgroups per slot
 constexpr int FEAT_WG = 128 / WG_PER_SLOT;         // hidden features per warpgroup
 constexpr int CHUNK = 16;                          // accumulator columns per tcgen05.ld
@@ -59,11 +60,7 @@ constexpr int EPI_WARPS = EPI_THREADS / 32;
 constexpr int THREADS = EPI_THREADS + 64;          // + the MMA warp + the fallback warp
 constexpr int MMA_WARP = EPI_WARPS;
 constexpr int FB_WARP = EPI_WARPS + 1;
-constexpr uint32_t ACT_BYTES = 128 * 128 * 2;      // one slot's BF16 activations
-constexpr uint32_t OFF_ACT = (MLP_IMG_BYTES + 1023) / 1024 * 1024;
-constexpr uint32_t OFF_ONES = OFF_ACT + SLOTS * ACT_BYTES;  // 128 x 16 BF16 A matrix
-constexpr uint32_t ONES_BYTES = 128 * 16 * 2;
-constexpr uint32_t OFF_BAR = OFF_ONES + ONES_BYTES;  // 1 weights + 3 mma-done + 3 epi-done
+constexpr uint32_t OFF_BAR = (MLP_IMG_BYTES + 127) / 128 * 128;  // 1 weights + 2 mma + 2 epi
 constexpr uint32_t OFF_SLOT = OFF_BAR + 8 * (1 + 2 * SLOTS);
 // fallback queue: indices of this CTA's particles outside the training
 // domain (-1 until written), then [0] the queue tail, [1] the number of
@@ -74,9 +71,13 @@ constexpr uint32_t OFF_FBC = OFF_FBQ + FBQ_CAP * 8;
 constexpr uint32_t SMEM_BYTES = (OFF_FBC + 8 + 127) / 128 * 128;
 static_assert(SMEM_BYTES <= 227 * 1024, "shared memory budget");
 static_assert(SMEM_BYTES > 114 * 1024, "one CTA per SM (it owns all tensor memory)");
-// Tensor memory: 128 FP32 accumulator columns per slot.
+// Tensor memory (columns): slot s holds its FP32 accumulator at 256 s and its
+// BF16 activations (the next MMA's A operand, 2 per column) at 256 s + 128;
+// the bias step's constant A matrix sits at 192.
 constexpr uint32_t TMEM_COLS = 512;
-static_assert(128 * SLOTS <= TMEM_COLS, "tensor memory budget");
+constexpr uint32_t TM_SLOT = 256, TM_ACT = 128, TM_ONES = 192;
+static_assert(TM_SLOT * (SLOTS - 1) + TM_ACT + 64 <= TMEM_COLS && TM_ONES + 8 <= TM_SLOT,
+              "tensor memory budget");
 
 // Two hidden pre-activations (FP32 accumulators r0, r1, bias included) ->
 // packed BF16 pair of 2*GELU: u = x (c0 + c1 x^2) in FP32x2, tanh.approx.f32,
@@ -100,19 +101,13 @@ BL_DEV uint32_t gelu2_pair(uint32_t r0, uint32_t r1) {
   return yb;
 }
 
-// GELU of CH consecutive accumulator columns (features f0 .. f0+CH-1 of one
-// particle row), written as CH/8 16-byte K chunks of the row in the
-// activation buffer (row base `row`, K chunks 128 bytes apart).
-template <int CH>
-BL_DEV void gelu_chunk(const uint32_t (&r)[CH], uint32_t row, int f0) {
-#pragma unroll
-  for (int q = 0; q < CH / 8; ++q) {
-    const uint32_t a = gelu2_pair(r[8 * q + 0], r[8 * q + 1]);
-    const uint32_t b = gelu2_pair(r[8 * q + 2], r[8 * q + 3]);
-    const uint32_t d = gelu2_pair(r[8 * q + 4], r[8 * q + 5]);
-    const uint32_t e = gelu2_pair(r[8 * q + 6], r[8 * q + 7]);
-    tc::st_shared_v4(row + (uint32_t)(f0 / 8 + q) * 128, a, b, d, e);
-  }
+// GELU of 16 consecutive accumulator columns (features f0 .. f0+15 of each
+// of the warp's 32 particle rows), written as 8 columns of packed BF16 pairs
+// at activation column f0 / 2 of the warp's lanes (base `t_act`).
+BL_DEV void gelu_chunk(const uint32_t (&r)[16], uint32_t t_act, int f0) {
+  tc::tmem_st8(t_act + (uint32_t)(f0 / 2), gelu2_pair(r[0], r[1]), gelu2_pair(r[2], r[3]),
+               gelu2_pair(r[4], r[5]), gelu2_pair(r[6], r[7]), gelu2_pair(r[8], r[9]),
+               gelu2_pair(r[10], r[11]), gelu2_pair(r[12], r[13]), gelu2_pair(r[14], r[15]));
 }
 
 // Registers: the 4 sub-partitions of the SM each hold a quarter of the 64K
@@ -143,10 +138,6 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
     tc::tmem_alloc(tc::smem_u32(tslot), TMEM_COLS);
     tc::tmem_relinquish();
   }
-  // constant A operand of the bias step: rows of (1, 1, 0, ..., 0), K-major
-  // core matrices (8 rows x 16 bytes, K chunks 128 bytes apart, row groups
-  // 256 bytes apart)
-  init_ones(smem, OFF_ONES, tid, THREADS);
   long long *fbq = reinterpret_cast<long long *>(smem + OFF_FBQ);
   int *fbc = reinterpret_cast<int *>(smem + OFF_FBC);
   for (int i = tid; i < FBQ_CAP; i += THREADS) fbq[i] = -1;
@@ -154,11 +145,21 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
     fbc[0] = 0;
     fbc[1] = 0;
   }
-  tc::fence_proxy_async();
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = *tslot;
+  // constant A operand of the bias step, in tensor memory: every row
+  // (1, 1, 0, ..., 0) over K = 16, i.e. one packed BF16 pair (1, 1) and seven
+  // zero columns; written by the four warps of the first warpgroup
+  if (warp < 4) {
+    tc::tmem_st8(tmem + ((uint32_t)(warp * 32) << 16) + TM_ONES, tc::pack_bf16x2(1.0f, 1.0f), 0u,
+                 0u, 0u, 0u, 0u, 0u, 0u);
+    tc::tmem_st_wait();
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
   if (tid == 0) load_weights(sbase, img, bar_w);
 
   if (warp == MMA_WARP) {
@@ -172,18 +173,15 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
       uint32_t ph = 0;  // bit s: expected phase of epi_done[s]
       constexpr uint32_t ID_H = tc::idesc_bf16(128, 128);
       constexpr uint32_t ID_O = tc::idesc_bf16(128, 16);
-      // descriptors of every operand; a K step adds 256 bytes (16 in the
-      // descriptor's address field, which cannot carry for a 228 KB space)
-      const uint64_t d_ones = tc::sdesc(sbase + OFF_ONES, 128, 256);
+      // shared-memory descriptors of the weights; a K step adds 256 bytes (16
+      // in the descriptor's address field, which cannot carry for a 228 KB space)
       const uint64_t d_w0 = tc::sdesc(sbase + OFF_W0, 128, 256);
       // layers 1..4: W1, W2, W3, W4 are MLP_IMG_WH bytes apart, and so are the
       // bias blocks B1..B4 at MLP_IMG_BH (the descriptor address is in 16 B units)
       const uint64_t d_w1 = tc::sdesc(sbase + OFF_W1, 128, 2048);
       const uint64_t d_b1 = tc::sdesc(sbase + OFF_B1, 128, 256);
-      // activation buffers: K = 16 layout for the input (layer 0), K = 128 after
-      const uint64_t d_in0 = tc::sdesc(sbase + OFF_ACT, 128, 256);
-      const uint64_t d_act0 = tc::sdesc(sbase + OFF_ACT, 128, 2048);
-      constexpr uint64_t ACT_STEP = ACT_BYTES >> 4;
+      // tensor-memory A operands: a K step of 16 BF16 is 8 columns
+      const uint32_t t_ones = tmem + TM_ONES;
       for (int64_t t0 = (int64_t)blockIdx.x * SLOTS; ok && t0 < ntiles;
            t0 += (int64_t)gridDim.x * SLOTS) {
         const int64_t live = ntiles - t0;  // slots s < live hold a tile in this pass
@@ -197,17 +195,17 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
               ph ^= 1u << s_;
               if (ok) {
                 tc::fence_after();
-                const uint32_t acc = tmem + 128 * s_;
+                const uint32_t acc = tmem + TM_SLOT * s_;
+                const uint32_t act = acc + TM_ACT;
                 if (l == 0) {
-                  tc::mma_ss(acc, d_in0 + s_ * ACT_STEP, d_w0, ID_H, 0);
+                  tc::mma_ts(acc, act, d_w0, ID_H, 0);
                 } else {
-                  const uint64_t da = d_act0 + s_ * ACT_STEP;
                   const uint64_t dw = d_w1 + (uint64_t)((l - 1) * (MLP_IMG_WH >> 4));
                   const uint64_t db = d_b1 + (uint64_t)((l - 1) * (MLP_IMG_BH >> 4));
                   const uint32_t id = (l < 4) ? ID_H : ID_O;
 #pragma unroll
-                  for (int j = 0; j < 8; ++j) tc::mma_ss(acc, da + 16 * j, dw + 16 * j, id, j > 0);
-                  tc::mma_ss(acc, d_ones, db, id, 1);
+                  for (int j = 0; j < 8; ++j) tc::mma_ts(acc, act + 8 * j, dw + 16 * j, id, j > 0);
+                  tc::mma_ts(acc, t_ones, db, id, 1);
                 }
                 tc::mma_commit(bar_w + 8 * (1 + s_));
               }
@@ -267,15 +265,13 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
     const int slot = wg / WG_PER_SLOT, h = wg % WG_PER_SLOT;
     const bool io = (h == 0);  // this warpgroup loads inputs and stores outputs
     const int m = wq * 32 + lane;  // this thread's particle row within a tile
-    const uint32_t t_acc = tmem + ((uint32_t)(wq * 32) << 16) + 128 * slot;
-    const uint32_t act = sbase + OFF_ACT + slot * ACT_BYTES;
-    const uint32_t row_in = act + (uint32_t)((m >> 3) * 256 + (m & 7) * 16);    // K = 16 layout
-    const uint32_t row_h = act + (uint32_t)((m >> 3) * 2048 + (m & 7) * 16);    // K = 128 layout
+    const uint32_t t_acc = tmem + ((uint32_t)(wq * 32) << 16) + TM_SLOT * slot;
+    const uint32_t t_act = t_acc + TM_ACT;  // this warp's lanes of the slot's activations
     const uint32_t my_mma = bar_w + 8 * (1 + slot), my_epi = bar_w + 8 * (1 + SLOTS + slot);
     bool ok = __all_sync(0xffffffffu, tc::mbar_wait(bar_w, 0, BL_DEVERR_TMA_TIMEOUT, err));
     uint32_t ph = 0;
-    auto done = [&]() {  // hand the activation buffer and the accumulator to the MMA warp
-      tc::fence_proxy_async();
+    auto done = [&]() {  // hand the activations and the accumulator to the MMA warp
+      tc::tmem_st_wait();
       tc::fence_before();
       mbar_arrive(my_epi);
     };
@@ -320,9 +316,8 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
         for (int c = 0; c < 6; ++c)
           xn[c] = df_normalise(xin[c], nrm.mu_in[c][0], nrm.mu_in[c][1], nrm.inv_sd_in[c][0],
                                nrm.inv_sd_in[c][1]);
-        tc::st_shared_v4(row_in, tc::pack_bf16x2(xn[0], xn[1]), tc::pack_bf16x2(xn[2], xn[3]),
-                         tc::pack_bf16x2(xn[4], xn[5]), tc::pack_bf16x2(1.0f, 1.0f));
-        tc::st_shared_v4(row_in + 128, 0u, 0u, 0u, 0u);
+        tc::tmem_st8(t_act, tc::pack_bf16x2(xn[0], xn[1]), tc::pack_bf16x2(xn[2], xn[3]),
+                     tc::pack_bf16x2(xn[4], xn[5]), tc::pack_bf16x2(1.0f, 1.0f), 0u, 0u, 0u, 0u);
       }
       done();  // layer 0 may start
       if (io) {  // prefetch this slot's next tile while the current one is in the network
@@ -344,10 +339,10 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
         for (int c = 0; c < FEAT_WG / CHUNK; c += 2) {
           const int f = f_base + c * CHUNK;
           tc::tmem_ld(t_acc + f + CHUNK, rb);
-          gelu_chunk<CHUNK>(ra, row_h, f);
+          gelu_chunk(ra, t_act, f);
           tc::tmem_ld_wait_regs(rb);
           if (c + 2 < FEAT_WG / CHUNK) tc::tmem_ld(t_acc + f + 2 * CHUNK, ra);
-          gelu_chunk<CHUNK>(rb, row_h, f + CHUNK);
+          gelu_chunk(rb, t_act, f + CHUNK);
           if (c + 2 < FEAT_WG / CHUNK) tc::tmem_ld_wait_regs(ra);
         }
         done();  // layer l+1 may read these activations and overwrite the accumulator

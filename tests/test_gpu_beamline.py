@@ -291,15 +291,17 @@ def test_batched_uneven_bunches_per_bunch_quads():
                         worst = max(worst, d)
                     else:
                         worst_small = max(worst_small, d)
-        # and the particles themselves, one by one (scaled by the rms of the
-        # largest bunch's output, which tiny bunches do not have of their own)
+        # and the particles themselves, one by one, scaled by the bunch's own
+        # output rms (each bunch has its own quadrupoles); bunches of a few
+        # particles take the first bunch's rms, having none of their own
         if counts[b]:
             if rms0 is None:
                 rms0 = [np.std(c) for c in zo]
             for c in range(6):
+                rms = np.std(zo[c]) if counts[b] >= 100 else rms0[c]
                 d = np.abs(got[c][sl] - zo[c])
-                dpart[c].append(d / rms0[c])
-                assert np.all(d <= 2e-3 * rms0[c] + 2.0 ** -6 * np.abs(zo[c]))
+                dpart[c].append(d / rms)
+                assert np.all(d <= 2e-3 * rms + 2.0 ** -6 * np.abs(zo[c]))
     dall = [np.concatenate(v) for v in dpart]
     worst_particle = max(float(np.median(v)) for v in dall)
     within = min(float(np.mean(v <= 2e-3)) for v in dall)
