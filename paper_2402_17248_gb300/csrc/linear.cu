@@ -115,13 +115,16 @@ stream_kernel(Soa<T> zin, Soa<T> zout, int64_t n, const int64_t *__restrict__ of
 namespace segk {
 constexpr int WARPS = 8;
 constexpr int THREADS = 32 * WARPS;
-constexpr int PPT = 2;                  // particles per thread and stage (two keep the
+constexpr int PPT = 2;                  // particles per thread and pass (two keep the
                                         // float-float sums within the register budget)
-constexpr int SUB = 128 * PPT;          // particles per ring stage
-constexpr int STAGES = 8;
-constexpr int MIN_SUB_PER_CTA = 4096 / SUB;  // a unit spans >= 4096 particles: at most as many
+constexpr int PASS = 128 * PPT;         // particles per pass of the block over a stage
+constexpr int PASSES = 4;               // passes per stage
+constexpr int SUB = PASS * PASSES;      // particles per ring stage
+constexpr int STAGES = 4;
+constexpr int MIN_SUB_PER_CTA = 4;      // a unit spans >= 4096 particles: at most as many
                                         // partial slots as the generic kernel's blocks
-constexpr int RENORM_SUBS = 32 / PPT;   // float-float renormalisation period (sub-chunks)
+static_assert(MIN_SUB_PER_CTA * SUB >= 4096, "unit");
+constexpr int RENORM_SUBS = 4;          // float-float renormalisation period (stages)
 constexpr uint32_t COORD_BYTES = SUB * 4;
 constexpr uint32_t STAGE_BYTES = 6 * COORD_BYTES;
 constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES;
@@ -300,6 +303,30 @@ BL_DEV void seg_load_map(float (&M)[18], float (&c)[6], const float *__restrict_
   for (int i = 0; i < 6; ++i) c[i] = centers ? __ldg(centers + (int64_t)b * 6 + i) : 0.0f;
 }
 
+// The warp is done reading ring stage s (sub-chunk j); the last warp to
+// release it refills it with sub-chunk j + STAGES once every warp's arrival
+// has completed the stage's empty phase.
+BL_DEV void seg_release(int s, int64_t j, int64_t nsub, int64_t r_hi, int64_t r_lo,
+                        const Soa<float> &zin, uint32_t sb, uint32_t full0, uint32_t empty0,
+                        int *s_cnt, long long *s_issued, unsigned *err, int lane) {
+  using namespace segk;
+  __syncwarp();
+  if (lane == 0) {
+    mbar_arrive_cta(empty0 + 8 * s);
+    if (atomicAdd(&s_cnt[s], 1) == WARPS - 1) {
+      s_cnt[s] = 0;
+      const int64_t jn = j + STAGES;
+      if (jn < nsub && tc::mbar_wait(empty0 + 8 * s, (uint32_t)((j / STAGES) & 1),
+                                     BL_DEVERR_TMA_TIMEOUT, err)) {
+        const int64_t qn = r_lo + jn * SUB;
+        seg_issue(zin, qn, min((int64_t)SUB, r_hi - qn), s, sb, full0 + 8 * s);
+        *s_issued = jn + 1;
+      }
+    }
+  }
+  __syncwarp();
+}
+
 template <int ROLE, bool APPLY, bool MOMENTS>
 BL_DEV void seg_consume(const Soa<float> &zin, Soa<float> &zout, int64_t n, int64_t r_lo,
                         int64_t r_hi, int64_t nsub, const int64_t *__restrict__ offsets,
@@ -320,6 +347,7 @@ BL_DEV void seg_consume(const Soa<float> &zin, Soa<float> &zout, int64_t n, int6
   int64_t pe = bunch_end(offsets, b, n);
   if (APPLY) seg_load_map<ROLE>(M, c, mats, per_bunch, centers, b);
   bool ok = true, open = false;
+  using V = typename VecOf<PPT>::type;
   for (int64_t j = 0; j < nsub; ++j) {
     const int s = (int)(j % STAGES);
     if (ok)
@@ -327,66 +355,88 @@ BL_DEV void seg_consume(const Soa<float> &zin, Soa<float> &zout, int64_t n, int6
                                                  BL_DEVERR_TMA_TIMEOUT, err));
     const int64_t q0 = r_lo + j * SUB, q1 = min(q0 + SUB, r_hi);
     const int cnt = (int)(q1 - q0), c4 = cnt & ~3;
-    const int64_t p0 = q0 + PPT * g;
-    float v[PPT][6];
-    if (PPT * g + PPT <= c4) {
-      using V = typename VecOf<PPT>::type;
-      const uint8_t *st = smem + s * STAGE_BYTES + 4 * PPT * g;
+    const uint8_t *st = smem + s * STAGE_BYTES + 4 * PPT * g;
+    if (cnt == SUB && pe >= q1) {
+      // the whole stage is full and inside bunch b: four passes, no masks
+#pragma unroll 1
+      for (int it = 0; it < PASSES; ++it) {
+        float v[PPT][6];
 #pragma unroll
-      for (int i = 0; i < 6; ++i) {
-        float w[PPT];
-        vec_get(*reinterpret_cast<const V *>(st + i * COORD_BYTES), w);
+        for (int i = 0; i < 6; ++i) {
+          float w[PPT];
+          vec_get(*reinterpret_cast<const V *>(st + i * COORD_BYTES + it * PASS * 4), w);
 #pragma unroll
-        for (int k = 0; k < PPT; ++k) v[k][i] = w[k];
+          for (int k = 0; k < PPT; ++k) v[k][i] = w[k];
+        }
+        if (it == PASSES - 1) seg_release(s, j, nsub, r_hi, r_lo, zin, sb, full0, empty0, s_cnt,
+                                          s_issued, err, lane);
+        seg_group<ROLE, APPLY, MOMENTS, false>(v, q0 + it * PASS + PPT * g, 0, 0, M, c, has_c,
+                                               shi, slo, nf, zout);
       }
-    } else {
-      // past the copied multiple of four (only the array's last particles)
-#pragma unroll
-      for (int k = 0; k < PPT; ++k)
-#pragma unroll
-        for (int i = 0; i < 6; ++i)
-          v[k][i] = (PPT * g + k >= c4 && PPT * g + k < cnt) ? zin.c[i][p0 + k] : 0.0f;
-    }
-    // release the stage; the last warp to do so refills it with sub-chunk
-    // j + STAGES once every warp's arrival has completed the empty phase
-    __syncwarp();
-    if (lane == 0) {
-      mbar_arrive_cta(empty0 + 8 * s);
-      if (atomicAdd(&s_cnt[s], 1) == WARPS - 1) {
-        s_cnt[s] = 0;
-        const int64_t jn = j + STAGES;
-        if (jn < nsub &&
-            tc::mbar_wait(empty0 + 8 * s, (uint32_t)((j / STAGES) & 1), BL_DEVERR_TMA_TIMEOUT,
-                          err)) {
-          const int64_t qn = r_lo + jn * SUB;
-          seg_issue(zin, qn, min((int64_t)SUB, r_hi - qn), s, sb, full0 + 8 * s);
-          *s_issued = jn + 1;
+      open = true;
+      if (pe == q1) {  // bunch b ends with this stage
+        if (MOMENTS) {
+          seg_flush<ROLE>(shi, slo, nf, red, partials + ((int64_t)b + blockIdx.x) * 28, warp, lane);
+          open = false;
+        }
+        if (b + 1 < n_bunch) {
+          ++b;
+          pe = bunch_end(offsets, b, n);
+          if (APPLY && (per_bunch || has_c)) seg_load_map<ROLE>(M, c, mats, per_bunch, centers, b);
         }
       }
-    }
-    // in place, the particles past the copied part are read from global
-    // memory: every warp reads them before any warp stores (last sub-chunk)
-    if (c4 < cnt) __syncthreads();
-    int64_t cur = q0;
-    for (;;) {
-      const int64_t hi = min(q1, pe);
-      if (hi > cur) {
-        if (cur == q0 && hi == q1 && cnt == SUB)
-          seg_group<ROLE, APPLY, MOMENTS, false>(v, p0, cur, hi, M, c, has_c, shi, slo, nf, zout);
-        else
-          seg_group<ROLE, APPLY, MOMENTS, true>(v, p0, cur, hi, M, c, has_c, shi, slo, nf, zout);
-        open = true;
+    } else {
+      // a stage with bunch boundaries or the array's ragged end: each pass
+      // walks the bunch pieces it meets, with masks
+      int64_t cur = q0;
+#pragma unroll 1
+      for (int it = 0; it < PASSES; ++it) {
+        const int64_t a0 = q0 + it * PASS;
+        if (a0 >= q1) break;
+        const int64_t a1 = min(a0 + PASS, q1);
+        const int64_t p0 = a0 + PPT * g;
+        const int rel = it * PASS + PPT * g;  // position of this thread's first particle in the stage
+        float v[PPT][6];
+        if (rel + PPT <= c4) {
+#pragma unroll
+          for (int i = 0; i < 6; ++i) {
+            float w[PPT];
+            vec_get(*reinterpret_cast<const V *>(st + i * COORD_BYTES + it * PASS * 4), w);
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) v[k][i] = w[k];
+          }
+        } else {
+          // past the copied multiple of four (only the array's last particles)
+#pragma unroll
+          for (int k = 0; k < PPT; ++k)
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+              v[k][i] = (rel + k >= c4 && rel + k < cnt) ? zin.c[i][p0 + k] : 0.0f;
+        }
+        // in place, the particles past the copied part come from global
+        // memory: every warp reads them before any warp stores
+        if (a1 > q0 + c4) __syncthreads();
+        for (;;) {
+          const int64_t hi = min(a1, pe);
+          if (hi > cur) {
+            seg_group<ROLE, APPLY, MOMENTS, true>(v, p0, cur, hi, M, c, has_c, shi, slo, nf, zout);
+            open = true;
+          }
+          if (hi < pe) break;  // bunch b goes on past this pass
+          if (MOMENTS && open) {
+            seg_flush<ROLE>(shi, slo, nf, red, partials + ((int64_t)b + blockIdx.x) * 28, warp,
+                            lane);
+            open = false;
+          }
+          if (++b >= n_bunch) break;
+          pe = bunch_end(offsets, b, n);
+          if (APPLY && (per_bunch || has_c)) seg_load_map<ROLE>(M, c, mats, per_bunch, centers, b);
+          cur = hi;
+          if (cur >= a1) break;
+        }
+        cur = max(cur, a1);
       }
-      if (hi < pe) break;  // bunch b goes on past this sub-chunk
-      if (MOMENTS && open) {
-        seg_flush<ROLE>(shi, slo, nf, red, partials + ((int64_t)b + blockIdx.x) * 28, warp, lane);
-        open = false;
-      }
-      if (++b >= n_bunch) break;
-      pe = bunch_end(offsets, b, n);
-      if (APPLY && (per_bunch || has_c)) seg_load_map<ROLE>(M, c, mats, per_bunch, centers, b);
-      cur = hi;
-      if (cur >= q1) break;
+      seg_release(s, j, nsub, r_hi, r_lo, zin, sb, full0, empty0, s_cnt, s_issued, err, lane);
     }
     if (MOMENTS && (j % RENORM_SUBS) == RENORM_SUBS - 1) {
 #pragma unroll

@@ -244,8 +244,8 @@ mlp_grad_kernel(Soa<float> zin, Soa<float> zout, const int64_t *__restrict__ idx
 __global__ void __launch_bounds__(256)
 reduce_adam_kernel(const float *__restrict__ part, int nblocks, const double *__restrict__ loss_part,
                    double inv_count6, float *__restrict__ params, float *__restrict__ m,
-                   float *__restrict__ v, float lr, float b1, float b2, float eps, float c1,
-                   float c2, float *loss_out, float *grad_out, int apply) {
+                   float *__restrict__ v, float lr, float b1, float b2, float omb1, float omb2,
+                   float eps, float c1, float c2, float *loss_out, float *grad_out, int apply) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0 && loss_out) {
     double t = 0.0;
@@ -257,8 +257,10 @@ reduce_adam_kernel(const float *__restrict__ part, int nblocks, const double *__
   for (int b = 0; b < nblocks; ++b) g += part[(int64_t)b * MLP_PSTRIDE + i];
   if (grad_out) grad_out[i] = g;
   if (!apply) return;
-  const float mi = fmaf(b1, m[i], (1.0f - b1) * g);
-  const float vi = fmaf(b2, v[i], (1.0f - b2) * g * g);
+  // omb1 = 1 - beta1 and omb2 = 1 - beta2 come from the host in FP64: formed
+  // in FP32 from the rounded beta2 = 0.999f, 1 - beta2 would be off by 1.3e-5
+  const float mi = fmaf(b1, m[i], omb1 * g);
+  const float vi = fmaf(b2, v[i], omb2 * g * g);
   m[i] = mi;
   v[i] = vi;
   const float mh = mi / c1, vh = vi / c2;
@@ -328,7 +330,8 @@ cudaError_t launch_mlp_reduce_adam(const float *partials, int nblocks, const dou
   const int apply = step > 0;
   reduce_adam_kernel<<<(MLP_NPARAM + 255) / 256, 256, 0, st>>>(
       partials, nblocks, loss_partials, 1.0 / (6.0 * (double)batch), params, m, v, (float)lr,
-      (float)b1, (float)b2, (float)eps, (float)(apply ? c1 : 1.0), (float)(apply ? c2 : 1.0),
+      (float)b1, (float)b2, (float)(1.0 - b1), (float)(1.0 - b2), (float)eps,
+      (float)(apply ? c1 : 1.0), (float)(apply ? c2 : 1.0),
       loss_out, grad_out, apply);
   return cudaGetLastError();
 }

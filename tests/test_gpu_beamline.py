@@ -301,13 +301,17 @@ def test_batched_uneven_bunches_per_bunch_quads():
                 rms = np.std(zo[c]) if counts[b] >= 100 else rms0[c]
                 d = np.abs(got[c][sl] - zo[c])
                 dpart[c].append(d / rms)
-                assert np.all(d <= 2e-3 * rms + 2.0 ** -6 * np.abs(zo[c]))
+                # a rounding flip of a BF16 activation moves a particle by a
+                # BF16 ulp of a value of the order of the coordinate's spread
+                assert np.all(d <= 2e-3 * rms + 2.0 ** -6 * (np.abs(zo[c]) + rms))
     dall = [np.concatenate(v) for v in dpart]
     worst_particle = max(float(np.median(v)) for v in dall)
+    largest = max(float(np.max(v)) for v in dall)
     within = min(float(np.mean(v <= 2e-3)) for v in dall)
     print("batched vs oracle: worst second-moment difference / (sd_a sd_b) %.3e (bunches "
           "> 1000 particles), %.3e (smaller); particles: worst median difference / rms %.3e, "
-          "fraction within 2e-3 rms %.5f" % (worst, worst_small, worst_particle, within))
+          "fraction within 2e-3 rms %.5f, largest %.2e" % (worst, worst_small, worst_particle,
+                                                           within, largest))
     assert within >= 0.99
     # downstream stages quantise their inputs to BF16; particles whose FP32
     # input lies within rounding of a BF16 midpoint move by one BF16 ulp, so

@@ -46,7 +46,9 @@ def _beamline(z, single_stage=False, lead_section=False):
     if lead_section:  # linear elements before the first stage: a segment in the chunked head
         # (millimetres: the beam's beta function at the entrance is ~4 mm)
         els = [lattice.drift(0.001), lattice.quad(0.001, 5.0), lattice.drift(0.001)] + els
-    return bl.Lattice(els), sur
+    lat = bl.Lattice(els)
+    lat.elements = els
+    return lat, sur
 
 
 def _device_reference(z, g, lat):
@@ -56,22 +58,39 @@ def _device_reference(z, g, lat):
     return [c.astype(np.float32) for c in from_bunch(b)], m, nf, b.gamma_ref
 
 
-def _moments_close(a, b):
-    """|a - b| <= 2e-10 x the entry's natural scale (N for the count, the
-    spread sigma_a for a mean, sigma_a sigma_b for a second moment S_ab):
-    each side is within the library's moment tolerance of 1e-10 of the exact
-    moments (float-float sums, grouped differently on the two sides), so
-    they differ by at most twice that"""
-    a, b = np.asarray(a), np.asarray(b)
-    sd = np.sqrt(np.abs(b[..., [7, 13, 18, 22, 25, 27]]))  # from the diagonal S_aa
+def _moments_close(a, b, lat, g, m_entry):
+    """|a - b| <= 2e-10 x the entry's natural scale. Each side reduces the
+    particles at a segment entry within the library's moment tolerance of
+    1e-10 of the exact moments (float-float sums, grouped differently on the
+    two sides), so the two reductions differ by at most 2e-10 sigma_a sigma_b
+    there (N for the count, sigma_a for a mean). Both sides then propagate
+    the reduced moments through the same FP64 element maps, so after
+    elements with cumulative map M the difference is M dS M^T, bounded by
+    2e-10 v_i v_j with v = |M| sigma (elementwise absolute value of M) and
+    sigma the spreads at the segment entry. m_entry: moments of the bunch at
+    the lattice entrance (the reduction of a leading segment)."""
+    from paper_2402_17248_gb300 import bl
+    a, b = np.asarray(a)[:, 0], np.asarray(b)[:, 0]
+    els = lat.elements
+    diag = [7, 13, 18, 22, 25, 27]
     scale = np.empty_like(b)
-    scale[..., 0] = b[..., 0]
-    scale[..., 1:7] = sd
-    j = 7
-    for p in range(6):
-        for q in range(p, 6):
-            scale[..., j] = sd[..., p] * sd[..., q]
-            j += 1
+    entry = np.asarray(m_entry)
+    gam, first = g, 0
+    for e, el in enumerate(els):
+        if el["kind"] == "plasma":
+            gam = bl.bl_reference_exit(el, gam)
+            M = np.eye(6)
+            entry, first = b[e], e + 1
+        else:
+            M = bl.bl_segment_matrix(els[first:e + 1], gam)
+        v = np.abs(M) @ np.sqrt(np.abs(entry[diag]))
+        scale[e, 0] = b[e, 0]
+        scale[e, 1:7] = v
+        j = 7
+        for p in range(6):
+            for q in range(p, 6):
+                scale[e, j] = v[p] * v[q]
+                j += 1
     err = np.abs(a - b) / (scale + 1e-300)
     print("pooled vs whole-bunch moments: max scaled difference %.2e" % np.max(err))
     return np.all(err <= 2e-10)
@@ -100,7 +119,8 @@ def test_host_stream_matches_device(n, chunk, single, lead):
         assert np.array_equal(a.numpy(), w, equal_nan=True)
     finite = np.isfinite(m_dev)
     assert np.array_equal(np.isfinite(m), finite)
-    assert _moments_close(np.where(finite, m, 0.0), np.where(finite, m_dev, 0.0))
+    assert _moments_close(np.where(finite, m, 0.0), np.where(finite, m_dev, 0.0), lat, g,
+                          bl.bl_moments(to_bunch(z, g))[0])
     # the inputs are untouched when the output is separate
     assert all(np.array_equal(a.numpy(), c) for a, c in zip(hin, z))
 
@@ -121,7 +141,9 @@ def test_host_stream_in_place_pageable_and_nonfinite():
         assert np.array_equal(a, w, equal_nan=True)
     finite = np.isfinite(m_dev)
     assert np.array_equal(np.isfinite(m), finite)
-    assert _moments_close(np.where(finite, m, 0.0), np.where(finite, m_dev, 0.0))
+    zc = [np.where(np.isfinite(c), c, 0.0).astype(np.float32) for c in z]
+    assert _moments_close(np.where(finite, m, 0.0), np.where(finite, m_dev, 0.0), lat, g,
+                          bl.bl_moments(to_bunch(zc, g))[0])
 
 
 def test_host_stream_without_moments_and_repeat():
