@@ -19,13 +19,18 @@ first stages, three of 700 for the later ones) use PReLU,
 prelu(x) = max(x, 0) + a min(x, 0) with one learned slope a per layer (the
 single-parameter form; reading). `forward(..., slopes=[a_0, ...])` selects it.
 
-Optional BF16 emulation rounds the network input and every hidden activation
-to bfloat16 (round to nearest even) at the points where a BF16 datapath
-stores them; all sums stay FP64.
+Optional BF16 emulation rounds at the points where a BF16 datapath stores
+values: the normalised network input is carried as a pair of bfloat16
+numbers, hi = bf16(x) and lo = bf16(x - hi) (16 significant bits; one BF16
+value alone would quantise the input to 2^-9, which the exit coordinates'
+strong dependence on the arrival time t turns into errors of percents of
+their spread), and every hidden activation is rounded to one bfloat16 value
+(round to nearest even); all sums stay FP64.
 
-Parity: forward and backward pinned against an independent float64 autograd
-implementation (torch CPU, test only) and central finite differences; GELU
-special values; Adam's first step closed form and an independent Adam.
+Parity: forward and backward (GELU and PReLU, the PReLU slopes' gradient
+included) pinned against an independent float64 autograd implementation
+(torch CPU, test only) and central finite differences; GELU special values;
+Adam's first step closed form and an independent Adam.
 """
 import math
 
@@ -63,12 +68,18 @@ def prelu(x, a):
     return np.where(x > 0.0, x, a * x)
 
 
+def bf16_pair(x):
+    """x carried as hi + lo with hi = bf16(x), lo = bf16(x - hi), as float64."""
+    hi = bf16_round(x)
+    return hi + bf16_round(np.asarray(x, dtype=np.float64) - hi)
+
+
 def forward(Ws, bs, X, bf16=False, keep=False, slopes=None):
     """X: (N, n_in) normalised inputs. Returns outputs (N, n_out) [, cache].
     slopes: None for GELU, else one PReLU slope per hidden layer."""
     h = np.asarray(X, dtype=np.float64)
     if bf16:
-        h = bf16_round(h)
+        h = bf16_pair(h)
     pre, acts = [], [h]
     nl = len(Ws)
     for l in range(nl):
@@ -86,25 +97,37 @@ def forward(Ws, bs, X, bf16=False, keep=False, slopes=None):
     return h
 
 
-def backward(Ws, cache, dY):
+def backward(Ws, cache, dY, slopes=None):
     """Reverse mode through the network for upstream gradient dY (N, n_out).
 
     Returns (dX, dWs, dbs): gradients with respect to the network input, the
     weights and the biases (summed over the batch). Rounding to bfloat16 in an
-    emulated forward is treated as the identity.
+    emulated forward is treated as the identity. With slopes (a PReLU
+    network), returns (dX, dWs, dbs, dslopes): d prelu / d pre = 1 where
+    pre > 0 and a otherwise, and d prelu / d a = min(pre, 0), so
+    dL/da_l = sum over the batch and the layer's units of min(pre, 0) times
+    the gradient with respect to that layer's output.
     """
     pre, acts = cache
     nl = len(Ws)
     dWs = [None] * nl
     dbs = [None] * nl
+    dsl = [0.0] * (nl - 1)
     d = np.asarray(dY, dtype=np.float64)
     for l in range(nl - 1, -1, -1):
         dWs[l] = d.T @ acts[l]
         dbs[l] = d.sum(axis=0)
         d = d @ Ws[l]
         if l > 0:
-            d = d * gelu_grad(pre[l - 1])
-    return d, dWs, dbs
+            z = pre[l - 1]
+            if slopes is None:
+                d = d * gelu_grad(z)
+            else:
+                dsl[l - 1] = float(np.sum(d * np.minimum(z, 0.0)))
+                d = d * np.where(z > 0.0, 1.0, slopes[l - 1])
+    if slopes is None:
+        return d, dWs, dbs
+    return d, dWs, dbs, dsl
 
 
 def mse(P, Y):

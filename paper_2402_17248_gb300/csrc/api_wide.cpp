@@ -63,6 +63,9 @@ bl_status bl_wide_mlp_create(const bl_wide_mlp_desc *d, bl_wide_mlp **out) {
           return set_error(BL_ERR_INVALID_ARG, "weights must be finite");
         }
         img[wide_weight_offset(n, k, ly.N_pad) / 2] = __float2bfloat16_rn(w);
+        // the first layer sees each input as a BF16 hi (column k) + lo
+        // (column 8 + k) pair sharing the weight
+        if (l == 0) img[wide_weight_offset(n, 8 + k, ly.N_pad) / 2] = __float2bfloat16_rn(w);
       }
     std::vector<float> bias(ly.N_pad, 0.0f);
     for (int n = 0; n < N; ++n) {

@@ -202,9 +202,9 @@ BL_DEV float4 vec_make(const float (&o)[4]) { return make_float4(o[0], o[1], o[2
 
 // One group of PPT particles of one role: moments of the inputs (masked to
 // [lo, hi) when MASK) and the role's three output rows.
-template <int ROLE, bool APPLY, bool MOMENTS, bool MASK>
+template <int ROLE, bool APPLY, bool MOMENTS, bool MASK, bool HAS_C>
 BL_DEV void seg_group(const float (&v)[segk::PPT][6], int64_t p0, int64_t lo, int64_t hi,
-                      const float (&M)[18], const float (&c)[6], bool has_c,
+                      const float (&M)[18], const float (&c)[6],
                       float (&shi)[ROLE ? 13 : 14], float (&slo)[ROLE ? 13 : 14], float &nf,
                       Soa<float> &zout) {
   constexpr int J0 = ROLE ? 14 : 0, J1 = ROLE ? 27 : 14;
@@ -233,7 +233,7 @@ BL_DEV void seg_group(const float (&v)[segk::PPT][6], int64_t p0, int64_t lo, in
       float d[6];
 #pragma unroll
       for (int i = 0; i < 6; ++i) d[i] = v[k][i];
-      if (has_c) {
+      if (HAS_C) {
 #pragma unroll
         for (int i = 0; i < 6; ++i) d[i] -= c[i];
       }
@@ -292,15 +292,15 @@ BL_DEV void seg_flush(float (&shi)[ROLE ? 13 : 14], float (&slo)[ROLE ? 13 : 14]
   __syncthreads();
 }
 
-// The role's three rows of bunch b's segment matrix and its centre.
-template <int ROLE>
+// The role's three rows of bunch b's segment matrix and (HAS_C) its centre.
+template <int ROLE, bool HAS_C>
 BL_DEV void seg_load_map(float (&M)[18], float (&c)[6], const float *__restrict__ mats,
                          int per_bunch, const float *__restrict__ centers, int b) {
   const float *Mb = mats + (per_bunch ? (int64_t)b * 36 : 0) + 18 * ROLE;
 #pragma unroll
   for (int i = 0; i < 18; ++i) M[i] = __ldg(Mb + i);
 #pragma unroll
-  for (int i = 0; i < 6; ++i) c[i] = centers ? __ldg(centers + (int64_t)b * 6 + i) : 0.0f;
+  for (int i = 0; i < 6; ++i) c[i] = HAS_C ? __ldg(centers + (int64_t)b * 6 + i) : 0.0f;
 }
 
 // The warp is done reading ring stage s (sub-chunk j); the last warp to
@@ -327,7 +327,7 @@ BL_DEV void seg_release(int s, int64_t j, int64_t nsub, int64_t r_hi, int64_t r_
   __syncwarp();
 }
 
-template <int ROLE, bool APPLY, bool MOMENTS>
+template <int ROLE, bool APPLY, bool MOMENTS, bool HAS_C>
 BL_DEV void seg_consume(const Soa<float> &zin, Soa<float> &zout, int64_t n, int64_t r_lo,
                         int64_t r_hi, int64_t nsub, const int64_t *__restrict__ offsets,
                         int n_bunch, const float *__restrict__ mats, int per_bunch,
@@ -342,10 +342,9 @@ BL_DEV void seg_consume(const Soa<float> &zin, Soa<float> &zout, int64_t n, int6
 #pragma unroll
   for (int i = 0; i < NJ; ++i) { shi[i] = 0.0f; slo[i] = 0.0f; }
   float M[18], c[6];
-  const bool has_c = APPLY && centers != nullptr;
   int b = find_bunch(offsets, n_bunch, r_lo);
   int64_t pe = bunch_end(offsets, b, n);
-  if (APPLY) seg_load_map<ROLE>(M, c, mats, per_bunch, centers, b);
+  if (APPLY) seg_load_map<ROLE, HAS_C>(M, c, mats, per_bunch, centers, b);
   bool ok = true, open = false;
   using V = typename VecOf<PPT>::type;
   for (int64_t j = 0; j < nsub; ++j) {
@@ -370,8 +369,8 @@ BL_DEV void seg_consume(const Soa<float> &zin, Soa<float> &zout, int64_t n, int6
         }
         if (it == PASSES - 1) seg_release(s, j, nsub, r_hi, r_lo, zin, sb, full0, empty0, s_cnt,
                                           s_issued, err, lane);
-        seg_group<ROLE, APPLY, MOMENTS, false>(v, q0 + it * PASS + PPT * g, 0, 0, M, c, has_c,
-                                               shi, slo, nf, zout);
+        seg_group<ROLE, APPLY, MOMENTS, false, HAS_C>(v, q0 + it * PASS + PPT * g, 0, 0, M, c,
+                                                      shi, slo, nf, zout);
       }
       open = true;
       if (pe == q1) {  // bunch b ends with this stage
@@ -382,7 +381,7 @@ BL_DEV void seg_consume(const Soa<float> &zin, Soa<float> &zout, int64_t n, int6
         if (b + 1 < n_bunch) {
           ++b;
           pe = bunch_end(offsets, b, n);
-          if (APPLY && (per_bunch || has_c)) seg_load_map<ROLE>(M, c, mats, per_bunch, centers, b);
+          if (APPLY && (per_bunch || HAS_C)) seg_load_map<ROLE, HAS_C>(M, c, mats, per_bunch, centers, b);
         }
       }
     } else {
@@ -419,7 +418,7 @@ BL_DEV void seg_consume(const Soa<float> &zin, Soa<float> &zout, int64_t n, int6
         for (;;) {
           const int64_t hi = min(a1, pe);
           if (hi > cur) {
-            seg_group<ROLE, APPLY, MOMENTS, true>(v, p0, cur, hi, M, c, has_c, shi, slo, nf, zout);
+            seg_group<ROLE, APPLY, MOMENTS, true, HAS_C>(v, p0, cur, hi, M, c, shi, slo, nf, zout);
             open = true;
           }
           if (hi < pe) break;  // bunch b goes on past this pass
@@ -430,7 +429,7 @@ BL_DEV void seg_consume(const Soa<float> &zin, Soa<float> &zout, int64_t n, int6
           }
           if (++b >= n_bunch) break;
           pe = bunch_end(offsets, b, n);
-          if (APPLY && (per_bunch || has_c)) seg_load_map<ROLE>(M, c, mats, per_bunch, centers, b);
+          if (APPLY && (per_bunch || HAS_C)) seg_load_map<ROLE, HAS_C>(M, c, mats, per_bunch, centers, b);
           cur = hi;
           if (cur >= a1) break;
         }
@@ -447,7 +446,7 @@ BL_DEV void seg_consume(const Soa<float> &zin, Soa<float> &zout, int64_t n, int6
     seg_flush<ROLE>(shi, slo, nf, red, partials + ((int64_t)b + blockIdx.x) * 28, warp, lane);
 }
 
-template <bool APPLY, bool MOMENTS>
+template <bool APPLY, bool MOMENTS, bool HAS_C>
 __global__ void __launch_bounds__(segk::THREADS, 2)
 seg_f32_kernel(Soa<float> zin, Soa<float> zout, int64_t n, int64_t per_cta,
                const int64_t *__restrict__ offsets, int n_bunch, const float *__restrict__ mats,
@@ -482,11 +481,11 @@ seg_f32_kernel(Soa<float> zin, Soa<float> zout, int64_t n, int64_t per_cta,
   }
   __syncthreads();
   if ((warp & 1) == 0)
-    seg_consume<0, APPLY, MOMENTS>(zin, zout, n, r_lo, r_hi, nsub, offsets, n_bunch, mats,
+    seg_consume<0, APPLY, MOMENTS, HAS_C>(zin, zout, n, r_lo, r_hi, nsub, offsets, n_bunch, mats,
                                    per_bunch, centers, partials, err, smem, sb, full0, empty0,
                                    s_cnt, &s_issued, red, warp, lane);
   else
-    seg_consume<1, APPLY, MOMENTS>(zin, zout, n, r_lo, r_hi, nsub, offsets, n_bunch, mats,
+    seg_consume<1, APPLY, MOMENTS, HAS_C>(zin, zout, n, r_lo, r_hi, nsub, offsets, n_bunch, mats,
                                    per_bunch, centers, partials, err, smem, sb, full0, empty0,
                                    s_cnt, &s_issued, red, warp, lane);
   // no copy may still be writing this CTA's shared memory when it exits (the
@@ -508,7 +507,7 @@ int64_t seg_per_cta(int64_t n, int num_sms) {
   return std::max<int64_t>(segk::MIN_SUB_PER_CTA, (S + G - 1) / G);
 }
 
-template <bool APPLY, bool MOMENTS>
+template <bool APPLY, bool MOMENTS, bool HAS_C>
 cudaError_t launch_seg(Soa<float> zin, Soa<float> zout, int64_t n, const int64_t *offsets,
                        int n_bunch, const float *mats, int per_bunch, const float *centers,
                        double *partials, int num_sms, unsigned *err, int64_t *unit,
@@ -522,7 +521,7 @@ cudaError_t launch_seg(Soa<float> zin, Soa<float> zout, int64_t n, const int64_t
   {
     std::lock_guard<std::mutex> lk(mu);
     if (!configured[dev]) {
-      e = cudaFuncSetAttribute(seg_f32_kernel<APPLY, MOMENTS>,
+      e = cudaFuncSetAttribute(seg_f32_kernel<APPLY, MOMENTS, HAS_C>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)segk::SMEM_BYTES);
       if (e != cudaSuccess) return e;
@@ -533,7 +532,7 @@ cudaError_t launch_seg(Soa<float> zin, Soa<float> zout, int64_t n, const int64_t
   const int64_t S = (n + segk::SUB - 1) / segk::SUB;
   const int64_t grid = (S + per - 1) / per;
   if (unit) *unit = per * segk::SUB;
-  seg_f32_kernel<APPLY, MOMENTS><<<(unsigned)grid, segk::THREADS, segk::SMEM_BYTES, st>>>(
+  seg_f32_kernel<APPLY, MOMENTS, HAS_C><<<(unsigned)grid, segk::THREADS, segk::SMEM_BYTES, st>>>(
       zin, zout, n, per, offsets, n_bunch, mats, per_bunch, centers, partials, err);
   return cudaGetLastError();
 }
@@ -552,17 +551,26 @@ cudaError_t launch_stream(Soa<T> zin, Soa<T> zout, int64_t n, const int64_t *off
   if (unit) *unit = STREAM_CHUNK;
   if (n <= 0) return cudaSuccess;
   if constexpr (sizeof(T) == 4) {
-    if (aligned16(zin) && aligned16(zout) && (apply || moments)) {
+    if (aligned16(zin) && aligned16(zout) && (apply || moments) &&
+        !(apply && moments && centers)) {
       DevCtx *ctx = nullptr;
       if (current_ctx(&ctx) != BL_OK) return cudaErrorInvalidDevice;
-      if (apply && moments)
-        return launch_seg<true, true>(zin, zout, n, offsets, n_bunch, mats, per_bunch, centers,
-                                      partials, ctx->num_sms, ctx->err_word, unit, st);
-      if (apply)
-        return launch_seg<true, false>(zin, zout, n, offsets, n_bunch, mats, per_bunch, centers,
-                                       partials, ctx->num_sms, ctx->err_word, unit, st);
-      return launch_seg<false, true>(zin, zout, n, offsets, n_bunch, mats, per_bunch, centers,
-                                     partials, ctx->num_sms, ctx->err_word, unit, st);
+      // the centres of the transposed maps (adjoint) never come with moments
+      if (apply && moments && !centers)
+        return launch_seg<true, true, false>(zin, zout, n, offsets, n_bunch, mats, per_bunch,
+                                             nullptr, partials, ctx->num_sms, ctx->err_word,
+                                             unit, st);
+      if (apply && !moments)
+        return centers ? launch_seg<true, false, true>(zin, zout, n, offsets, n_bunch, mats,
+                                                       per_bunch, centers, partials, ctx->num_sms,
+                                                       ctx->err_word, unit, st)
+                       : launch_seg<true, false, false>(zin, zout, n, offsets, n_bunch, mats,
+                                                        per_bunch, nullptr, partials,
+                                                        ctx->num_sms, ctx->err_word, unit, st);
+      if (!apply)
+        return launch_seg<false, true, false>(zin, zout, n, offsets, n_bunch, mats, per_bunch,
+                                              nullptr, partials, ctx->num_sms, ctx->err_word,
+                                              unit, st);
     }
   }
   const int64_t nb = stream_blocks(n);

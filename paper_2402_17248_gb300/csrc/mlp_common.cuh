@@ -58,6 +58,28 @@ BL_DEV float df_affine(float y, float sh, float sl, float mh, float ml) {
   return __fadd_rn(s, __fadd_rn(__fadd_rn(se, pe), fmaf(y, sl, ml)));
 }
 
+// The K = 16 input row of the first layer as 8 packed BF16 pairs: columns
+// 0..5 the BF16 high parts of the 6 normalised inputs, 6 and 7 the constant
+// 1 that multiplies the bias hi/lo weights, 8..13 the inputs' low parts
+// bf16(x - hi), 14 and 15 zero. The first layer's weights repeat in columns
+// 8..13, so the MMA sees each input with 16 significant bits.
+BL_DEV void input_row(const float (&xn)[6], uint32_t (&w)[8]) {
+  float hi[6], lo[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    hi[c] = __bfloat162float(__float2bfloat16_rn(xn[c]));
+    lo[c] = __fsub_rn(xn[c], hi[c]);
+  }
+  w[0] = tc::pack_bf16x2(hi[0], hi[1]);
+  w[1] = tc::pack_bf16x2(hi[2], hi[3]);
+  w[2] = tc::pack_bf16x2(hi[4], hi[5]);
+  w[3] = tc::pack_bf16x2(1.0f, 1.0f);
+  w[4] = tc::pack_bf16x2(lo[0], lo[1]);
+  w[5] = tc::pack_bf16x2(lo[2], lo[3]);
+  w[6] = tc::pack_bf16x2(lo[4], lo[5]);
+  w[7] = 0u;
+}
+
 BL_DEV void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }

@@ -310,14 +310,15 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
           }
         }
       }
-      if (io) {  // normalised BF16 input row; bias hi/lo columns k = 6, 7; k = 8..15 zero
+      if (io) {  // normalised input row (K = 16, see input_row)
         float xn[6];
 #pragma unroll
         for (int c = 0; c < 6; ++c)
           xn[c] = df_normalise(xin[c], nrm.mu_in[c][0], nrm.mu_in[c][1], nrm.inv_sd_in[c][0],
                                nrm.inv_sd_in[c][1]);
-        tc::tmem_st8(t_act, tc::pack_bf16x2(xn[0], xn[1]), tc::pack_bf16x2(xn[2], xn[3]),
-                     tc::pack_bf16x2(xn[4], xn[5]), tc::pack_bf16x2(1.0f, 1.0f), 0u, 0u, 0u, 0u);
+        uint32_t w[8];
+        input_row(xn, w);
+        tc::tmem_st8(t_act, w[0], w[1], w[2], w[3], w[4], w[5], w[6], w[7]);
       }
       done();  // layer 0 may start
       if (io) {  // prefetch this slot's next tile while the current one is in the network
@@ -385,11 +386,14 @@ __global__ void mlp_pack_kernel(const float *__restrict__ P, uint8_t *__restrict
   const int stride = gridDim.x * blockDim.x;
   __nv_bfloat16 *im = reinterpret_cast<__nv_bfloat16 *>(img);
   const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
-  // layer 0: N = 128, K = 16 (6 inputs, bias hi/lo at columns 6 and 7, zeros)
+  // layer 0: N = 128, K = 16: the weights of the 6 inputs' BF16 high parts
+  // (columns 0..5), the bias hi/lo (6, 7), the same weights again for the
+  // inputs' low parts (8..13), zeros
   for (int i = tid; i < 128 * 16; i += stride) {
     const int nn = i / 16, k = i % 16;
     __nv_bfloat16 v = zero;
     if (k < 6) v = __float2bfloat16_rn(P[0 + nn * 6 + k]);
+    else if (k >= 8 && k < 14) v = __float2bfloat16_rn(P[0 + nn * 6 + (k - 8)]);
     else if (k < 8) {
       __nv_bfloat16 hi, lo;
       split_bf16(P[768 + nn], hi, lo);

@@ -45,7 +45,7 @@ BL_DEV void gelu_fwd(float x, float &y, float &dy) {
 }
 
 struct Smem {
-  float h0[S][8];          // normalised input (BF16-rounded)
+  float h0[S][8];          // normalised input (BF16 hi + lo)
   float h[4][S][128];      // h_1..h_4 (BF16-rounded GELU outputs)
   float dg[4][S][128];     // GELU'(a_0..a_3)
   float d[S][128];         // current delta (dL/da_l)
@@ -68,13 +68,16 @@ mlp_grad_kernel(Soa<float> zin, Soa<float> zout, const int64_t *__restrict__ idx
   const int64_t s0 = (int64_t)blockIdx.x * S;
   const int ns = (count - s0 < S) ? (int)(count - s0) : S;
 
-  // ---- inputs: FP64 normalisation, BF16 rounding (zero rows past the end)
+  // ---- inputs: FP64 normalisation, carried as a BF16 hi + lo pair as on
+  // the tensor-core path (zero rows past the end)
   for (int i = tid; i < S * 8; i += NT) {
     const int s = i / 8, c = i % 8;
     float v = 0.f;
     if (s < ns && c < 6) {
       const int64_t col = idx ? idx[s0 + s] : s0 + s;
-      v = bf16r((float)(((double)zin.c[c][col] - nrm.mu_in[c]) * nrm.inv_sd_in[c]));
+      const float x = (float)(((double)zin.c[c][col] - nrm.mu_in[c]) * nrm.inv_sd_in[c]);
+      const float hi = bf16r(x);
+      v = __fadd_rn(hi, bf16r(__fsub_rn(x, hi)));
     }
     sm.h0[s][c] = v;
   }

@@ -374,13 +374,13 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_train_tc_kernel(TrainArgs a, u
           tgt[c] = df_normalise(o, a.nrm.mu_out[c][0], a.nrm.mu_out[c][1], a.inv_sd_out[c][0],
                                 a.inv_sd_out[c][1]);
         }
-        const uint4 v4 = make_uint4(tc::pack_bf16x2(xn[0], xn[1]), tc::pack_bf16x2(xn[2], xn[3]),
-                                    tc::pack_bf16x2(xn[4], xn[5]), tc::pack_bf16x2(1.0f, 1.0f));
-        tc::st_shared_v4(in_row, v4.x, v4.y, v4.z, v4.w);
-        tc::st_shared_v4(in_row + 128, 0u, 0u, 0u, 0u);
+        uint32_t w[8];
+        input_row(xn, w);
+        tc::st_shared_v4(in_row, w[0], w[1], w[2], w[3]);
+        tc::st_shared_v4(in_row + 128, w[4], w[5], w[6], w[7]);
         uint8_t *g0 = scr + (m >> 3) * 256 + (m & 7) * 16;
-        *reinterpret_cast<uint4 *>(g0) = v4;
-        *reinterpret_cast<uint4 *>(g0 + 128) = make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4 *>(g0) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4 *>(g0 + 128) = make_uint4(w[4], w[5], w[6], w[7]);
       }
       done();
       // ---- forward, hidden layers 0..2 (activations kept, h' in TMEM)
@@ -557,16 +557,18 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_train_tc_kernel(TrainArgs a, u
         done();
       }
       if (!ok) break;
-      // ---- dW0 and db0 readout (columns 0..5: the inputs; column 6: the
-      // bias, whose K column holds 1) and the tile's loss
+      // ---- dW0 and db0 readout (columns 0..5 and 8..13: the inputs' high
+      // and low parts, which share each weight; column 6: the bias, whose K
+      // column holds 1) and the tile's loss
       wait_mma();
       if (!ok) break;
       if (io) {
-        uint32_t r[8];
-        tc::tmem_ld8(t_row + COL_DW, r);
+        uint32_t r[16];
+        tc::tmem_ld16(t_row + COL_DW, r);
         tc::tmem_ld_wait_regs(r);
 #pragma unroll
-        for (int k = 0; k < 6; ++k) P[woff(0) + m * 6 + k] = __uint_as_float(r[k]);
+        for (int k = 0; k < 6; ++k)
+          P[woff(0) + m * 6 + k] = __fadd_rn(__uint_as_float(r[k]), __uint_as_float(r[8 + k]));
         P[boff(0) + m] = __uint_as_float(r[6]);
       }
       if (tid == 0) a.loss_part[t] = red_loss[0] + red_loss[1] + red_loss[2] + red_loss[3];

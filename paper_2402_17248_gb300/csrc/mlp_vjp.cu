@@ -228,9 +228,10 @@ mlp_vjp_kernel(Soa<float> zin, Soa<float> lam, int64_t n, int64_t ntiles,
         for (int c = 0; c < 6; ++c)
           xn[c] = df_normalise(valid ? zin.c[c][p] : 0.0f, nrm.mu_in[c][0], nrm.mu_in[c][1],
                                nrm.inv_sd_in[c][0], nrm.inv_sd_in[c][1]);
-        tc::st_shared_v4(row_in, tc::pack_bf16x2(xn[0], xn[1]), tc::pack_bf16x2(xn[2], xn[3]),
-                         tc::pack_bf16x2(xn[4], xn[5]), tc::pack_bf16x2(1.0f, 1.0f));
-        tc::st_shared_v4(row_in + 128, 0u, 0u, 0u, 0u);
+        uint32_t w[8];
+        input_row(xn, w);
+        tc::st_shared_v4(row_in, w[0], w[1], w[2], w[3]);
+        tc::st_shared_v4(row_in + 128, w[4], w[5], w[6], w[7]);
       }
       done();
       // ---- forward: hidden layers 0..2 (activations and h' kept)

@@ -218,8 +218,10 @@ __global__ void __launch_bounds__(THREADS, 1) wide_layer_kernel(WideLayer p, uns
   if (warp == 1) tc::tmem_dealloc(tmem, TMEM_COLS);
 }
 
-// Normalised BF16 network input of a chunk: one 64-column K tile per 128
-// particles, columns 0..5 the coordinates, the rest zero.
+// Normalised network input of a chunk: one 64-column K tile per 128
+// particles, columns 0..5 the coordinates' BF16 high parts and 8..13 their
+// low parts bf16(x - hi) (the first layer's weights repeat there), the rest
+// zero.
 __global__ void __launch_bounds__(256) wide_prep_kernel(Soa<float> z, int64_t n, int RT,
                                                         uint8_t *A, MlpNormF nrm) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -231,11 +233,12 @@ __global__ void __launch_bounds__(256) wide_prep_kernel(Soa<float> z, int64_t n,
                         nrm.inv_sd_in[c][0], nrm.inv_sd_in[c][1]);
   uint8_t *t = A + (size_t)(i / BM) * A_TILE;
   const int r = (int)(i % BM);
-  *reinterpret_cast<uint4 *>(t + tile_off(r, 0)) =
-      make_uint4(tc::pack_bf16x2(x[0], x[1]), tc::pack_bf16x2(x[2], x[3]),
-                 tc::pack_bf16x2(x[4], x[5]), 0u);
+  uint32_t w[8];
+  input_row(x, w);
+  *reinterpret_cast<uint4 *>(t + tile_off(r, 0)) = make_uint4(w[0], w[1], w[2], 0u);
+  *reinterpret_cast<uint4 *>(t + tile_off(r, 8)) = make_uint4(w[4], w[5], w[6], 0u);
 #pragma unroll
-  for (int k = 8; k < BK; k += 8)
+  for (int k = 16; k < BK; k += 8)
     *reinterpret_cast<uint4 *>(t + tile_off(r, k)) = make_uint4(0u, 0u, 0u, 0u);
 }
 

@@ -97,6 +97,13 @@ def test_bf16_round_matches_torch():
     # ties go to even: 1 + 2^-8 is halfway between 1 and 1 + 2^-7
     assert mlp.bf16_round(np.array([1 + 2.0 ** -8]))[0] == 1.0
     assert mlp.bf16_round(np.array([1 + 3 * 2.0 ** -8]))[0] == 1 + 2.0 ** -6
+    # the input pair hi + lo: exact for 16 significant bits, 2^-16 relative beyond
+    x = np.array([1 + 2.0 ** -10, 1 + 2.0 ** -10 + 2.0 ** -20, -3.0 * (1 + 2.0 ** -12), 0.75])
+    p = mlp.bf16_pair(x)
+    assert p[0] == x[0] and p[2] == x[2] and p[3] == x[3]
+    assert p[1] == 1 + 2.0 ** -10
+    r = np.random.default_rng(4).normal(size=10000) * 3
+    assert np.max(np.abs(mlp.bf16_pair(r) - r) / np.abs(r)) <= 2.0 ** -16
 
 
 def test_identity_layers():
@@ -157,9 +164,12 @@ def test_prelu_network_matches_torch():
         if l < len(Ws) - 1:
             h = torch.nn.functional.prelu(h, torch.tensor([slopes[l]], dtype=torch.float64))
     assert np.max(np.abs(Y - h.numpy())) < 1e-13
-    # BF16 emulation: round the input and every hidden activation
+    # BF16 emulation: the input as a BF16 hi + lo pair, every hidden
+    # activation rounded once
     Yb = mlp.forward(Ws, bs, X, bf16=True, slopes=slopes)
-    h = torch.tensor(X).to(torch.bfloat16).double()
+    tx = torch.tensor(X)
+    hi = tx.to(torch.bfloat16).double()
+    h = hi + (tx - hi).to(torch.bfloat16).double()
     for l, (W, b) in enumerate(zip(Ws, bs)):
         h = h @ torch.tensor(W).T + torch.tensor(b)
         if l < len(Ws) - 1:
@@ -168,3 +178,41 @@ def test_prelu_network_matches_torch():
     assert np.max(np.abs(Yb - h.numpy())) < 1e-13
     # closed form on special values
     assert np.array_equal(mlp.prelu(np.array([-2.0, 0.0, 3.0]), 0.25), np.array([-0.5, 0.0, 3.0]))
+
+
+def test_prelu_backward_matches_torch_autograd_and_differences():
+    """PReLU reverse mode (weights, biases, input and the per-layer slopes)
+    against torch float64 autograd through torch's prelu, and the slope
+    gradient against central differences of the network output."""
+    Ws, bs = _net(seed=8, widths=[6, 24, 24, 24, 6])
+    slopes = [0.25, -0.1, 0.6]
+    rng = np.random.default_rng(9)
+    X = rng.normal(size=(41, 6))
+    dY = rng.normal(size=(41, 6))
+    Y, cache = mlp.forward(Ws, bs, X, keep=True, slopes=slopes)
+    dX, dWs, dbs, dsl = mlp.backward(Ws, cache, dY, slopes=slopes)
+    tW = [torch.tensor(W, requires_grad=True) for W in Ws]
+    tb = [torch.tensor(b, requires_grad=True) for b in bs]
+    ta = [torch.tensor([a], dtype=torch.float64, requires_grad=True) for a in slopes]
+    tX = torch.tensor(X, requires_grad=True)
+    h = tX
+    for l in range(len(Ws)):
+        h = h @ tW[l].T + tb[l]
+        if l < len(Ws) - 1:
+            h = torch.nn.functional.prelu(h, ta[l])
+    h.backward(torch.tensor(dY))
+    assert np.max(np.abs(dX - tX.grad.numpy())) < 1e-13
+    for a, b in zip(dWs, tW):
+        assert np.max(np.abs(a - b.grad.numpy())) < 1e-12
+    for a, b in zip(dbs, tb):
+        assert np.max(np.abs(a - b.grad.numpy())) < 1e-12
+    for a, b in zip(dsl, ta):
+        assert abs(a - b.grad.item()) < 1e-11 * max(1.0, abs(a))
+    eps = 1e-6
+    for l in range(3):
+        sp, sm = list(slopes), list(slopes)
+        sp[l] += eps
+        sm[l] -= eps
+        fd = (np.sum(mlp.forward(Ws, bs, X, slopes=sp) * dY)
+              - np.sum(mlp.forward(Ws, bs, X, slopes=sm) * dY)) / (2 * eps)
+        assert abs(fd - dsl[l]) < 1e-7 * max(1.0, abs(fd))
