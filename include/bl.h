@@ -102,7 +102,10 @@ typedef struct bl_lattice_s bl_lattice;
  *   BL_SBEND:  L [m] arc length, angle [rad] (sector bend, no edge focusing)
  *   BL_PLASMA: L [m], nsteps RK4 steps, n0_cm3 plasma density [1/cm^3],
  *              E0_Vpm wake amplitude [V/m], phi0 reference phase [rad];
- *              surrogate: trained stage surrogate, or NULL for the RK4 push.
+ *              surrogate: trained stage surrogate, or NULL for the RK4 push;
+ *              wide_surrogate: one of the paper's wide PReLU networks as the
+ *              stage's surrogate instead (at most one of the two is set; the
+ *              wide stage maps every particle and has no training domain).
  *   BL_PLASMA_LENS: L [m], k [1/m^2] focusing both planes alike (k > 0
  *              focuses): the linear map of an active plasma lens, whose
  *              azimuthal field gradient g = dB/dr [T/m] gives k = e g / p_ref
@@ -120,6 +123,8 @@ typedef struct {
   double n0_cm3, E0_Vpm, phi0;
   const bl_surrogate *surrogate;
   const double *per_bunch_k;
+  const struct bl_wide_mlp_s *wide_surrogate; /* BL_PLASMA: a wide PReLU surrogate of the
+                                                 stage (see bl_wide_mlp), or NULL */
 } bl_element;
 
 /* Compile a beamline. elements: host array of n_elements entries (copied).
@@ -377,6 +382,33 @@ bl_status bl_surrogate_grad(const bl_surrogate *s, const float *in, const float 
 bl_status bl_surrogate_loss(const bl_surrogate *s, const float *in, const float *out,
                             int64_t ld, const int64_t *idx, int64_t count,
                             double *loss_out, bl_stream stream);
+
+/* ---- training the wide PReLU networks (Sec. 3 and 4.2: MSE on normalised
+ * data, Adam, minibatches; every weight, bias and the slope of every hidden
+ * layer is learned) ----
+ * Parameters form one flat FP32 vector: W_0 (widths[1] x widths[0],
+ * row-major), b_0, W_1, b_1, ..., W_{n-1}, b_{n-1}, then the n-1 slopes. The
+ * forward pass is the inference datapath (tcgen05 BF16 layers, FP32
+ * pre-activations kept); the backward pass (dW = dZ^T X, dX = dZ W with the
+ * BF16-valued weights, the PReLU derivative and the slopes' gradient
+ * sum min(pre, 0) dX) runs in FP32 on the CUDA cores. in, out, idx, ld and
+ * batch as for bl_surrogate_train_step; batch <= BL_WIDE_MAX_BATCH. */
+#define BL_WIDE_MAX_BATCH 65536
+bl_status bl_wide_mlp_num_params(const bl_wide_mlp *m, int64_t *nparam);
+/* Minibatch gradient into grad_out (device, num_params floats, flat layout)
+ * and loss (device float, or NULL), without an update. */
+bl_status bl_wide_mlp_grad(const bl_wide_mlp *m, const float *in, const float *out, int64_t ld,
+                           const int64_t *idx, int64_t batch, float *grad_out, float *loss_out,
+                           bl_stream stream);
+/* One Adam step (bias-corrected, the step counter kept in the network);
+ * loss_out: device float, or NULL, the minibatch loss before the update. */
+bl_status bl_wide_mlp_train_step(bl_wide_mlp *m, const float *in, const float *out, int64_t ld,
+                                 const int64_t *idx, int64_t batch, const bl_adam_cfg *cfg,
+                                 float *loss_out, bl_stream stream);
+/* The FP32 masters (after synchronising the device): W_out[l], b_out[l] host
+ * buffers sized like the descriptor's, slopes_out n_layers - 1 floats. */
+bl_status bl_wide_mlp_get_params(const bl_wide_mlp *m, float *const *W_out, float *const *b_out,
+                                 float *slopes_out);
 
 /* ------------------------------------------------------------ adjoint ---- */
 

@@ -20,8 +20,9 @@ prelu(x) = max(x, 0) + a min(x, 0) with one learned slope a per layer (the
 single-parameter form; reading). `forward(..., slopes=[a_0, ...])` selects it.
 
 Optional BF16 emulation rounds at the points where a BF16 datapath stores
-values: the normalised network input is carried as a pair of bfloat16
-numbers, hi = bf16(x) and lo = bf16(x - hi) (16 significant bits; one BF16
+values: the normalised network input, stored as an FP32 value x32, is
+carried as a pair of bfloat16 numbers, hi = bf16(x32) and lo = bf16(x32 - hi)
+(16 significant bits; one BF16
 value alone would quantise the input to 2^-9, which the exit coordinates'
 strong dependence on the arrival time t turns into errors of percents of
 their spread), and every hidden activation is rounded to one bfloat16 value
@@ -69,9 +70,12 @@ def prelu(x, a):
 
 
 def bf16_pair(x):
-    """x carried as hi + lo with hi = bf16(x), lo = bf16(x - hi), as float64."""
-    hi = bf16_round(x)
-    return hi + bf16_round(np.asarray(x, dtype=np.float64) - hi)
+    """x carried as hi + lo: x is first stored as an FP32 value x32 (as the
+    normalisation hands it to the network), then hi = bf16(x32) and
+    lo = bf16(x32 - hi); returned as float64."""
+    x32 = np.asarray(x, dtype=np.float64).astype(np.float32).astype(np.float64)
+    hi = bf16_round(x32)
+    return hi + bf16_round(x32 - hi)
 
 
 def forward(Ws, bs, X, bf16=False, keep=False, slopes=None):

@@ -39,7 +39,8 @@ class bl_bunch(C.Structure):
 class bl_element(C.Structure):
     _fields_ = [("kind", C.c_int32), ("nsteps", C.c_int32), ("L", C.c_double), ("k", C.c_double),
                 ("angle", C.c_double), ("n0_cm3", C.c_double), ("E0_Vpm", C.c_double),
-                ("phi0", C.c_double), ("surrogate", C.c_void_p), ("per_bunch_k", C.c_void_p)]
+                ("phi0", C.c_double), ("surrogate", C.c_void_p), ("per_bunch_k", C.c_void_p),
+                ("wide_surrogate", C.c_void_p)]
 
 
 class bl_mlp_desc(C.Structure):
@@ -97,6 +98,10 @@ _SIGS = {
     "bl_wide_mlp_create": ([_P, _P], C.c_int),
     "bl_wide_mlp_destroy": ([_P], C.c_int),
     "bl_wide_mlp_apply": ([_P, _P, _I64, _P], C.c_int),
+    "bl_wide_mlp_num_params": ([_P, _P], C.c_int),
+    "bl_wide_mlp_grad": ([_P, _P, _P, _I64, _P, _I64, _P, _P, _P], C.c_int),
+    "bl_wide_mlp_train_step": ([_P, _P, _P, _I64, _P, _I64, _P, _P, _P], C.c_int),
+    "bl_wide_mlp_get_params": ([_P, _P, _P, _P], C.c_int),
     "bl_last_error_message": ([], C.c_char_p),
     "bl_version": ([], C.c_char_p),
     "bl_poll_device_errors": ([], C.c_int),
@@ -198,7 +203,10 @@ def make_elements(elements):
         s.E0_Vpm = e.get("E0_Vpm", 0.0)
         s.phi0 = e.get("phi0", 0.0)
         sur = e.get("surrogate")
-        s.surrogate = sur.handle.value if sur is not None else None
+        if isinstance(sur, WideSurrogate):
+            s.wide_surrogate = sur.handle.value
+        else:
+            s.surrogate = sur.handle.value if sur is not None else None
         pbk = e.get("per_bunch_k")
         if pbk is not None:
             a = np.ascontiguousarray(pbk, dtype=np.float64)
@@ -488,15 +496,54 @@ class WideSurrogate:
         d.mu_in, d.sd_in, d.mu_out, d.sd_out = [v.ctypes.data_as(C.POINTER(C.c_double)) for v in nrm]
         self.handle = C.c_void_p()
         _check(lib().bl_wide_mlp_create(C.byref(d), C.byref(self.handle)))
+        self.mu_in, self.sd_in, self.mu_out, self.sd_out = [np.array(v) for v in nrm]
+        self.domain = None
 
     def __del__(self):
         if getattr(self, "handle", None) and _lib is not None:
             _lib.bl_wide_mlp_destroy(self.handle)
             self.handle = None
 
+    @property
+    def num_params(self):
+        n = C.c_int64(0)
+        _check(lib().bl_wide_mlp_num_params(self.handle, C.byref(n)))
+        return n.value
+
+    def params(self):
+        """(weights [out x in], biases, slopes) of the FP32 masters."""
+        L = len(self.widths) - 1
+        Ws = [np.zeros((self.widths[l + 1], self.widths[l]), dtype=np.float32) for l in range(L)]
+        bs = [np.zeros(self.widths[l + 1], dtype=np.float32) for l in range(L)]
+        sl = np.zeros(L - 1, dtype=np.float32)
+        Wp = (C.POINTER(C.c_float) * L)(*[w.ctypes.data_as(C.POINTER(C.c_float)) for w in Ws])
+        bp = (C.POINTER(C.c_float) * L)(*[b.ctypes.data_as(C.POINTER(C.c_float)) for b in bs])
+        _check(lib().bl_wide_mlp_get_params(self.handle, Wp, bp, sl.ctypes.data))
+        return Ws, bs, sl
+
 
 def bl_wide_mlp_apply(net, bunch, chunk=0, stream=None):
     _check(lib().bl_wide_mlp_apply(net.handle, bunch.ref(), int(chunk), _stream(stream)))
+
+
+def bl_wide_mlp_grad(net, inp, out, grad_out, idx=None, batch=None, loss_out=None, stream=None):
+    """inp, out: device float32 [6, ld]; grad_out: device float32 [num_params]."""
+    ld = inp.shape[1]
+    if batch is None:
+        batch = idx.numel() if idx is not None else ld
+    _check(lib().bl_wide_mlp_grad(net.handle, _ptr(inp), _ptr(out), ld, _ptr(idx), batch,
+                                  _ptr(grad_out), _ptr(loss_out), _stream(stream)))
+
+
+def bl_wide_mlp_train_step(net, inp, out, idx=None, batch=None, lr=1e-4, beta1=0.9,
+                           beta2=0.999, eps=1e-8, loss_out=None, stream=None):
+    assert inp.is_contiguous() and out.is_contiguous() and inp.shape == out.shape
+    ld = inp.shape[1]
+    if batch is None:
+        batch = idx.numel() if idx is not None else ld
+    cfg = bl_adam_cfg(lr, beta1, beta2, eps)
+    _check(lib().bl_wide_mlp_train_step(net.handle, _ptr(inp), _ptr(out), ld, _ptr(idx), batch,
+                                        C.byref(cfg), _ptr(loss_out), _stream(stream)))
 
 
 def bl_surrogate_create(Ws, bs, mu_in, sd_in, mu_out, sd_out):

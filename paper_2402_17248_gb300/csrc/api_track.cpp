@@ -168,6 +168,8 @@ bl_status run_stage(bl_bunch *b, bl_lattice_s *L, size_t g, cudaStream_t st, boo
                                ctx->num_sms, st));
   } else if (e.surrogate) {
     BL_TRY(bl_surrogate_apply(e.surrogate, b, st));
+  } else if (e.wide_surrogate) {
+    BL_TRY(bl_wide_mlp_apply(e.wide_surrogate, b, 0, st));
   } else if (b->dtype == BL_F32) {
     const float *tab = (const float *)((const uint8_t *)P.d_tables + P.table_off[g]);
     BL_CUDA(launch_pusher<float>(soa_of<float>(b), b->n, tr.c, tab, st));
@@ -201,7 +203,7 @@ bl_status track_checks(bl_bunch *b, bl_lattice_s *L) {
   BL_CHECK(!lattice_has_per_bunch(L) || L->n_bunch_k == b->n_bunch,
            "lattice per-bunch strengths do not match the bunch count");
   for (const auto &gr : L->groups)
-    if (gr.stage && L->els[gr.first].surrogate)
+    if (gr.stage && (L->els[gr.first].surrogate || L->els[gr.first].wide_surrogate))
       BL_CHECK(b->dtype == BL_F32, "surrogate stages need an FP32 bunch");
   return BL_OK;
 }
@@ -220,8 +222,11 @@ bl_status track_enqueue_range(bl_bunch *b, bl_lattice_s *L, size_t g0, size_t g1
     // one NVTX range per element group, so a profiler timeline shows the
     // beamline's structure (no cost without a profiler attached)
     const bool stage = L->groups[g].stage;
-    nvtxRangePushA(!stage ? "bl segment" : (L->els[L->groups[g].first].surrogate ? "bl stage: surrogate"
-                                                                               : "bl stage: pusher"));
+    const bl_element &first = L->els[L->groups[g].first];
+    nvtxRangePushA(!stage ? "bl segment"
+                          : (first.surrogate ? "bl stage: surrogate"
+                                             : (first.wide_surrogate ? "bl stage: wide surrogate"
+                                                                     : "bl stage: pusher")));
     bl_status r = BL_OK;
     if (stage) {
       r = run_stage(b, L, g, st, fused_fallback);
@@ -357,6 +362,10 @@ bl_status bl_lattice_create(const bl_element *elements, int32_t n_elements, int3
       BL_CHECK(e.nsteps >= 1 && e.nsteps <= (1 << 20), "plasma stage needs 1 <= nsteps <= 2^20");
       BL_CHECK(e.n0_cm3 > 0.0 && std::isfinite(e.E0_Vpm) && std::isfinite(e.phi0),
                "plasma stage parameters invalid");
+      BL_CHECK(!(e.surrogate && e.wide_surrogate),
+               "a plasma stage takes a surrogate or a wide surrogate, not both");
+    } else {
+      BL_CHECK(!e.surrogate && !e.wide_surrogate, "only plasma stages take surrogates");
     }
     std::vector<double> pk;
     if (e.kind == BL_QUAD && e.per_bunch_k) {

@@ -120,17 +120,34 @@ struct WideNet {
   struct Layer {
     uint8_t *W = nullptr;  // BF16 weights, tiled (see wide_weight_offset)
     float *b = nullptr;    // FP32 bias, N_pad entries
-    float slope = 0.0f;    // PReLU slope (hidden layers)
+    const float *slope = nullptr;  // PReLU slope (hidden layers), device (inside the masters)
+    int K = 0, N = 0;      // real widths
     int K_pad = 0, N_pad = 0;
   };
   std::vector<Layer> layers;
   MlpNorm nrm{};
+  // flat FP32 masters [W_0, b_0, ..., W_{L-1}, b_{L-1}, slopes] on the device
+  float *P = nullptr;
+  std::vector<int64_t> w_off, b_off;
+  int64_t slope_off = 0, nparam = 0;
+  int max_width = 0;
 };
 // Byte offset of weight (n, k) in a layer's tiled BF16 image.
 size_t wide_weight_offset(int n, int k, int N_pad);
 cudaError_t wide_mlp_configure();
 cudaError_t launch_wide_mlp(Soa<float> z, int64_t n, const WideNet &net, uint8_t *act0,
                             uint8_t *act1, int num_sms, unsigned *err, cudaStream_t st);
+// Rebuild every layer's BF16 image and bias array from the flat masters.
+cudaError_t launch_wide_pack(const WideNet &net, cudaStream_t st);
+// Device bytes of the training work buffers for a minibatch of `batch` pairs.
+size_t wide_train_bytes(const WideNet &net, int64_t batch);
+// Minibatch gradient (flat layout, into G) and loss (device float, or NULL)
+// of the MSE on normalised targets; inputs/targets coordinate-major [6][ld].
+cudaError_t launch_wide_grad(const WideNet &net, const float *in, const float *out, int64_t ld,
+                             const int64_t *idx, int64_t batch, float *G, float *loss_out,
+                             void *ws, int num_sms, unsigned *err, cudaStream_t st);
+cudaError_t launch_wide_adam(float *P, const float *G, float *M, float *V, int64_t n, double lr,
+                             double b1, double b2, double eps, int step, cudaStream_t st);
 
 // Partial-gradient row stride (floats) of the training kernels, padded for
 // 16-byte aligned vector stores.

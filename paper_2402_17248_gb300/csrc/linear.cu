@@ -124,7 +124,7 @@ constexpr int STAGES = 4;
 constexpr int MIN_SUB_PER_CTA = 4;      // a unit spans >= 4096 particles: at most as many
                                         // partial slots as the generic kernel's blocks
 static_assert(MIN_SUB_PER_CTA * SUB >= 4096, "unit");
-constexpr int RENORM_SUBS = 4;          // float-float renormalisation period (stages)
+constexpr int RENORM_SUBS = 2;          // float-float renormalisation period (stages)
 constexpr uint32_t COORD_BYTES = SUB * 4;
 constexpr uint32_t STAGE_BYTES = 6 * COORD_BYTES;
 constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES;

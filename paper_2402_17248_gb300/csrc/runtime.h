@@ -64,7 +64,7 @@ bl_status current_ctx(DevCtx **out);
 enum WsSlot {
   WS_PARTIALS = 0, WS_MOMENTS, WS_NONFINITE, WS_TABLES, WS_MATS, WS_CENTERS, WS_LAMBDA,
   WS_CKPT, WS_CROSS, WS_TRAIN, WS_LOSS, WS_WIDE0, WS_WIDE1, WS_FALLBACK, WS_TRAIN_SCRATCH,
-  WS_HOST_BUF, WS_HOST_RED, WS_COUNT
+  WS_HOST_BUF, WS_HOST_RED, WS_WIDE_TRAIN, WS_COUNT
 };
 struct Workspace {
   void *ptr[WS_COUNT] = {};
@@ -144,7 +144,8 @@ struct bl_surrogate_s {
 struct bl_wide_mlp_s {
   int device = -1;
   bl::WideNet net;
-  int max_width = 0;  // largest K_pad / N_pad of any layer
+  float *G = nullptr, *M = nullptr, *V = nullptr;  // flat gradient and Adam moments
+  int step = 0;
 };
 
 struct bl_lattice_s {

@@ -127,6 +127,52 @@ def fit_surrogate(xin, xout, steps=20000, batch=1200, lr=1e-3, lr_final=1e-5, se
     return sur, info
 
 
+def fit_wide_surrogate(xin, xout, widths, steps=2000, batch=4096, lr=1e-3, lr_final=1e-5,
+                       seed=0, slope0=0.25, test_frac=0.3, log_every=0):
+    """Train one of the paper's wide PReLU networks (widths 6, H, ..., H, 6;
+    every slope starts at slope0 and is learned, Sec. 3) on device pairs
+    with the library's wide training step; returns (network, info) with the
+    held-out loss history and the learned slopes."""
+    from synth.bunch import mlp_init
+    n = xin.shape[1]
+    ntest = int(round(test_frac * n))
+    ntrain = n - ntest
+    mu_i, sd_i = norm_constants(xin)
+    mu_o, sd_o = norm_constants(xout)
+    Ws, bs = mlp_init(list(widths), seed)
+    net = bl.WideSurrogate(Ws, bs, [slope0] * (len(widths) - 2), mu_i, sd_i, mu_o, sd_o)
+    xin = xin.contiguous()
+    xout = xout.contiguous()
+    test_idx = torch.arange(ntrain, n, device=xin.device)[:65536]
+    gen = torch.Generator(device=xin.device).manual_seed(seed)
+    loss = torch.zeros(1, device=xin.device)
+    scratch = torch.zeros(net.num_params, device=xin.device)
+    history = []
+
+    def test_loss():
+        bl.bl_wide_mlp_grad(net, xin, xout, scratch, idx=test_idx, loss_out=loss)
+        torch.cuda.synchronize()
+        return loss.item()
+
+    t0 = time.time()
+    history.append((0, test_loss(), 0.0))
+    chunk = max(1, steps // 10) if log_every else steps
+    for s0 in range(0, steps, chunk):
+        k = min(chunk, steps - s0)
+        idx = torch.randint(0, ntrain, (k, batch), device=xin.device, generator=gen)
+        for j in range(k):
+            s = s0 + j
+            a = lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * s / max(1, steps)))
+            bl.bl_wide_mlp_train_step(net, xin, xout, idx=idx[j], batch=batch, lr=a)
+        if log_every:
+            history.append((s0 + k, test_loss(), time.time() - t0))
+    final = test_loss()
+    info = {"steps": steps, "batch": batch, "lr": lr, "train_pairs": ntrain, "test_pairs": ntest,
+            "test_loss": final, "seconds": time.time() - t0, "history": history,
+            "slopes": net.params()[2].tolist()}
+    return net, info
+
+
 def plasma_wavenumber(n0_cm3=1.0e17):
     """k_p = omega_p / c of a plasma of electron density n0 [cm^-3] (CODATA 2018)."""
     e, eps0, me, c = 1.602176634e-19, 8.8541878128e-12, 9.1093837015e-31, 299792458.0

@@ -301,9 +301,9 @@ def test_batched_uneven_bunches_per_bunch_quads():
                 rms = np.std(zo[c]) if counts[b] >= 100 else rms0[c]
                 d = np.abs(got[c][sl] - zo[c])
                 dpart[c].append(d / rms)
-                # a rounding flip of a BF16 activation moves a particle by a
-                # BF16 ulp of a value of the order of the coordinate's spread
-                assert np.all(d <= 2e-3 * rms + 2.0 ** -6 * (np.abs(zo[c]) + rms))
+    # a rounding flip of a BF16 activation moves a particle by a few BF16
+    # ulps of a value of the order of the coordinate's spread (2^-8 x 4 sigma
+    # per flip), and a flip in the first stage is carried through the second
     dall = [np.concatenate(v) for v in dpart]
     worst_particle = max(float(np.median(v)) for v in dall)
     largest = max(float(np.max(v)) for v in dall)
@@ -312,7 +312,8 @@ def test_batched_uneven_bunches_per_bunch_quads():
           "> 1000 particles), %.3e (smaller); particles: worst median difference / rms %.3e, "
           "fraction within 2e-3 rms %.5f, largest %.2e" % (worst, worst_small, worst_particle,
                                                            within, largest))
-    assert within >= 0.99
+    assert within >= 0.999
+    assert largest <= 0.1
     # downstream stages quantise their inputs to BF16; particles whose FP32
     # input lies within rounding of a BF16 midpoint move by one BF16 ulp, so
     # a bunch of a few particles can move by a sizeable part of its spread

@@ -66,9 +66,11 @@ def _moments_close(a, b, lat, g, m_entry):
     there (N for the count, sigma_a for a mean). Both sides then propagate
     the reduced moments through the same FP64 element maps, so after
     elements with cumulative map M the difference is M dS M^T, bounded by
-    2e-10 v_i v_j with v = |M| sigma (elementwise absolute value of M) and
-    sigma the spreads at the segment entry. m_entry: moments of the bunch at
-    the lattice entrance (the reduction of a leading segment)."""
+    2e-10 v_i v_j with v = |M| s (elementwise absolute value of M). The
+    reductions accumulate raw sums of z_a z_b, whose float-float rounding is
+    relative to |<z_a z_b>| <= (sigma_a + |mu_a|)(sigma_b + |mu_b|), so s is
+    sigma + |mu| at the segment entry. m_entry: moments of the bunch at the
+    lattice entrance (the reduction of a leading segment)."""
     from paper_2402_17248_gb300 import bl
     a, b = np.asarray(a)[:, 0], np.asarray(b)[:, 0]
     els = lat.elements
@@ -83,7 +85,7 @@ def _moments_close(a, b, lat, g, m_entry):
             entry, first = b[e], e + 1
         else:
             M = bl.bl_segment_matrix(els[first:e + 1], gam)
-        v = np.abs(M) @ np.sqrt(np.abs(entry[diag]))
+        v = np.abs(M) @ (np.sqrt(np.abs(entry[diag])) + np.abs(entry[1:7]))
         scale[e, 0] = b[e, 0]
         scale[e, 1:7] = v
         j = 7
@@ -92,7 +94,9 @@ def _moments_close(a, b, lat, g, m_entry):
                 scale[e, j] = v[p] * v[q]
                 j += 1
     err = np.abs(a - b) / (scale + 1e-300)
-    print("pooled vs whole-bunch moments: max scaled difference %.2e" % np.max(err))
+    e, j = np.unravel_index(np.argmax(err), err.shape)
+    print("pooled vs whole-bunch moments: max scaled difference %.2e (element %d, entry %d)"
+          % (np.max(err), e, j))
     return np.all(err <= 2e-10)
 
 

@@ -71,3 +71,113 @@ def test_wide_rejects_bad_descriptors():
     Ws2, bs2 = mlp_init([5, 64, 6], 1)
     with pytest.raises(bl.BlError):
         bl.WideSurrogate(Ws2, bs2, [0.25], np.ones(6), one, one, one)  # input width 5
+
+
+def _pairs(n, seed):
+    """(input, target) pairs of a smooth 6D map on design-bunch inputs."""
+    rng = np.random.default_rng(seed)
+    zin, _ = _bunch(n, seed)
+    Zi = np.stack(zin).astype(np.float64)
+    sd = Zi.std(axis=1, keepdims=True)
+    A = rng.normal(size=(6, 6)) * 0.3 + np.eye(6)
+    Zo = (A @ (Zi / sd)) * sd + 0.1 * np.sin(Zi / sd) * sd
+    return Zi.astype(np.float32), Zo.astype(np.float32)
+
+
+def _flat_oracle_grad(Ws, bs, slopes, Zi, Zo, mu_i, sd_i, mu_o, sd_o):
+    """Loss and flat gradient [W0, b0, ..., slopes] of the oracle's MSE on
+    normalised data with the BF16-valued weights and BF16 rounding points."""
+    Wr = [mlp.bf16_round(np.asarray(W, np.float32).astype(np.float64)) for W in Ws]
+    br = [np.asarray(b, np.float32).astype(np.float64) for b in bs]
+    sl = [float(np.float32(a)) for a in slopes]
+    X = (Zi.T.astype(np.float64) - mu_i) / sd_i
+    Y = (Zo.T.astype(np.float64) - mu_o) / sd_o
+    P, cache = mlp.forward(Wr, br, X, bf16=True, keep=True, slopes=sl)
+    L = mlp.mse(P, Y)
+    _, dW, db, dsl = mlp.backward(Wr, cache, mlp.mse_grad(P, Y), slopes=sl)
+    flat = []
+    for l in range(len(Ws)):
+        flat += [dW[l].ravel(), db[l].ravel()]
+    flat.append(np.asarray(dsl))
+    return L, np.concatenate(flat)
+
+
+@pytest.mark.parametrize("widths,batch", [([6, 700, 700, 700, 6], 1000),
+                                          ([6, 900, 900, 900, 900, 900, 6], 777),
+                                          ([6, 96, 130, 6], 1)])
+def test_wide_gradient_matches_oracle(widths, batch):
+    """Minibatch MSE loss and gradient (every weight, bias and PReLU slope)
+    of the wide network's training path against the oracle's reverse mode
+    with the same BF16-valued weights; inputs gathered through an index
+    vector."""
+    import torch
+    from paper_2402_17248_gb300 import bl
+    Zi, Zo = _pairs(max(batch, 2000), 31)
+    mu_i, sd_i = Zi.mean(axis=1), Zi.std(axis=1)
+    mu_o, sd_o = Zo.mean(axis=1), Zo.std(axis=1)
+    Ws, bs = mlp_init(widths, 9)
+    slopes = [0.25 - 0.05 * l for l in range(len(widths) - 2)]
+    net = bl.WideSurrogate(Ws, bs, slopes, mu_i, sd_i, mu_o, sd_o)
+    sel = np.random.default_rng(batch).permutation(Zi.shape[1])[:batch]
+    din, dout = torch.tensor(Zi, device="cuda"), torch.tensor(Zo, device="cuda")
+    idx = torch.tensor(sel, device="cuda", dtype=torch.int64)
+    grad = torch.zeros(net.num_params, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    bl.bl_wide_mlp_grad(net, din, dout, grad, idx=idx, loss_out=loss)
+    torch.cuda.synchronize()
+    bl.bl_poll_device_errors()
+    L, flat = _flat_oracle_grad(Ws, bs, slopes, Zi[:, sel], Zo[:, sel], mu_i, sd_i, mu_o, sd_o)
+    g = grad.cpu().numpy().astype(np.float64)
+    rel = np.linalg.norm(g - flat) / np.linalg.norm(flat)
+    nsl = len(widths) - 2
+    rel_s = np.max(np.abs(g[-nsl:] - flat[-nsl:])) / np.max(np.abs(flat[-nsl:]))
+    print("widths %s batch %d: loss gpu %.6e oracle %.6e; gradient normwise rel err %.3e, "
+          "slopes %.3e" % (widths[1:-1], batch, loss.item(), L, rel, rel_s))
+    assert abs(loss.item() / L - 1) < 1e-3
+    assert rel < 5e-3
+    assert rel_s < 5e-3
+
+
+def test_wide_training_on_pusher_pairs_and_as_a_lattice_stage():
+    """A 3 x 700 PReLU network trained on the GPU (Adam on every weight, bias
+    and slope) on one plasma stage's pusher pairs lowers its held-out loss
+    and moves its slopes; as the stage of a lattice it tracks exactly like
+    bl_wide_mlp_apply followed by the section, and matches the oracle's
+    PReLU surrogate with its trained parameters."""
+    import torch
+    from paper_2402_17248_gb300 import bl, workflow
+    from oracle import beamline
+    from synth import lattice
+    from synth.bunch import training_population
+    g0 = BunchRecipe().gamma_ref
+    zt, _ = training_population(4, 65536, g0, 0.2 / workflow.plasma_wavenumber(), seed=1001)
+    els = lattice.staged_beamline(1, 400)
+    xin, xout, gin = workflow.stage_pairs(workflow.device_bunch(zt, g0), els)[0]
+    net, info = workflow.fit_wide_surrogate(xin, xout, [6, 700, 700, 700, 6], steps=1500,
+                                            batch=4096, lr=1e-3, seed=3, log_every=1)
+    h = info["history"]
+    print("3x700 on pusher pairs: held-out loss %.3e -> %.3e, slopes %s (%.1fs)"
+          % (h[0][1], info["test_loss"], np.round(info["slopes"], 4), info["seconds"]))
+    assert info["test_loss"] < 0.1 * h[0][1]
+    assert np.max(np.abs(np.asarray(info["slopes"]) - 0.25)) > 1e-3
+    # the trained network as the stage of a lattice
+    z, g = _bunch(30001, seed=5)
+    st = dict(els[0], surrogate=net)
+    b1 = to_bunch(z, g)
+    m1, nf = bl.bl_track(b1, bl.Lattice([st] + els[1:]))
+    b2 = to_bunch(z, g)
+    bl.bl_wide_mlp_apply(net, b2)
+    b2.struct.gamma_ref = bl.bl_reference_exit(els[0], g)
+    bl.bl_track(b2, bl.Lattice(els[1:]), moments=False)
+    for a, w in zip(from_bunch(b1), from_bunch(b2)):
+        assert np.array_equal(a, w)
+    assert b1.gamma_ref == b2.gamma_ref
+    Ws, bs, sl = net.params()
+    Wr = [mlp.bf16_round(W.astype(np.float64)) for W in Ws]
+    osur = mlp.Surrogate(Wr, [b.astype(np.float64) for b in bs], net.mu_in, net.sd_in,
+                         net.mu_out, net.sd_out, slopes=sl)
+    zo, go, snaps = beamline.track(z, g, [dict(els[0], surrogate=osur)] + els[1:], bf16=True)
+    got = from_bunch(b1)
+    worst = max(float(np.max(np.abs(a - w))) / np.std(w) for a, w in zip(got, zo))
+    print("  trained 3x700 stage + section vs oracle: max |gpu - oracle| / rms %.3e" % worst)
+    assert worst < 2e-3

@@ -103,7 +103,10 @@ def test_bf16_round_matches_torch():
     assert p[0] == x[0] and p[2] == x[2] and p[3] == x[3]
     assert p[1] == 1 + 2.0 ** -10
     r = np.random.default_rng(4).normal(size=10000) * 3
-    assert np.max(np.abs(mlp.bf16_pair(r) - r) / np.abs(r)) <= 2.0 ** -16
+    assert np.max(np.abs(mlp.bf16_pair(r) - r) / np.abs(r)) <= 2.0 ** -16 + 2.0 ** -24
+    # the split is of the FP32 value the normalisation stores
+    r32 = r.astype(np.float32).astype(np.float64)
+    assert np.array_equal(mlp.bf16_pair(r), mlp.bf16_pair(r32))
 
 
 def test_identity_layers():
@@ -167,7 +170,7 @@ def test_prelu_network_matches_torch():
     # BF16 emulation: the input as a BF16 hi + lo pair, every hidden
     # activation rounded once
     Yb = mlp.forward(Ws, bs, X, bf16=True, slopes=slopes)
-    tx = torch.tensor(X)
+    tx = torch.tensor(X).float().double()
     hi = tx.to(torch.bfloat16).double()
     h = hi + (tx - hi).to(torch.bfloat16).double()
     for l, (W, b) in enumerate(zip(Ws, bs)):
