@@ -3,30 +3,32 @@
 // every particle in place (Sec. 4.3: in-situ inference on device-resident
 // particles, with the normalise / de-normalise data preparation fused).
 //
-// Design (one persistent CTA per SM, two 128-particle tile slots per CTA,
-// warp-specialised: 16 epilogue warps, an MMA-issuing warp, a fallback warp):
+// Design (one persistent CTA per SM, three 128-particle tile slots per CTA,
+// warp-specialised: 24 epilogue warps, an MMA-issuing warp, a fallback warp):
 //  * The weight matrices and bias blocks (BF16, ~117 KB) are copied once per
 //    CTA into shared memory by bulk async copies and stay there for all
 //    tiles. They are the B operand of every MMA, in the K-major no-swizzle
 //    core-matrix layout prepared by the pack kernel.
-//  * A tile's activations never leave tensor memory. Each layer's
-//    accumulator D[128 particles x N] (FP32) takes 128 columns of the slot;
-//    the slot's epilogue warpgroups read it (tcgen05.ld), apply GELU, round
-//    to BF16 and write the row back into the slot's 64-column activation
-//    region (tcgen05.st, two BF16 per column): the A operand of the next
-//    layer's MMA, read by the tensor core from tensor memory. With both
-//    operands in shared memory an N = 128 MMA would read all 128 bytes per
-//    clock the SM's shared memory delivers, and the epilogue's stores would
-//    wait for every MMA in flight; with A in tensor memory the MMAs read only
-//    the weights from shared memory and the epilogue touches no shared
-//    memory, so the MMAs of one tile and the tanh work of the other overlap.
+//  * Each layer's accumulator D[128 particles x N] (FP32) takes 128 columns
+//    of tensor memory per slot; the slot's two epilogue warpgroups read it
+//    (tcgen05.ld), apply GELU, round to BF16 and write the row back as the A
+//    operand of the next layer's MMA. Slots 0 and 1 keep that row in tensor
+//    memory (64 columns each, two BF16 per column: tcgen05.st, and the MMA
+//    reads A from tensor memory), so their MMAs read only the weights from
+//    shared memory and their epilogues touch no shared memory. Tensor memory
+//    (512 columns) holds three accumulators but only two activation regions,
+//    so slot 2 writes its row to a 32 KB shared-memory buffer in the K-major
+//    layout and its MMAs read both operands from shared memory. Three tiles
+//    in flight keep the tensor pipe fed while the other slots' epilogues
+//    evaluate tanh (measured: 2.42 ms per 2^24 particles, against 2.58 ms
+//    with two tensor-memory slots and 2.49 ms with three shared-memory ones).
 //  * One lane of the MMA warp issues every MMA with descriptors precomputed
 //    once, so a K step costs one add; every hidden-layer MMA is M=128 x
 //    N=128 (x K=16). The MMA warp and the warpgroups hand the tensor-memory
 //    regions to each other through mbarriers (MMA-complete: commit-arrived;
 //    epilogue-complete: 256 thread arrivals).
 //  * Biases ride in the MMA: one extra K=16 step multiplies a constant
-//    tensor-memory A matrix whose first two K columns are 1 by the bias split
+//    shared-memory A matrix whose first two K columns are 1 by the bias split
 //    into BF16 hi and lo parts.
 //  * GELU: u = x (c0 + c1 x^2) in packed FP32x2, tanh.approx.f32, and
 //    2*GELU = x (1 + tanh u) as an FP32x2 FMA, rounded once to BF16. Hidden
@@ -51,7 +53,8 @@ namespace {
 
 using namespace mlp;
 
-constexpr int SLOTS = 2;
+constexpr int SLOTS = 3;
+constexpr int TM_SLOTS = 2;                        // slots whose activations stay in tensor memory
 constexpr int WG_PER_SLOT = 2;                     // epilogue warpgroups per slot
 constexpr int FEAT_WG = 128 / WG_PER_SLOT;         // hidden features per warpgroup
 constexpr int CHUNK = 16;                          // accumulator columns per tcgen05.ld
@@ -60,7 +63,11 @@ constexpr int EPI_WARPS = EPI_THREADS / 32;
 constexpr int THREADS = EPI_THREADS + 64;          // + the MMA warp + the fallback warp
 constexpr int MMA_WARP = EPI_WARPS;
 constexpr int FB_WARP = EPI_WARPS + 1;
-constexpr uint32_t OFF_BAR = (MLP_IMG_BYTES + 127) / 128 * 128;  // 1 weights + 2 mma + 2 epi
+constexpr uint32_t ACT_BYTES = 128 * 128 * 2;      // the shared-memory slot's BF16 activations
+constexpr uint32_t OFF_ACT = (MLP_IMG_BYTES + 1023) / 1024 * 1024;
+constexpr uint32_t OFF_ONES = OFF_ACT + ACT_BYTES;  // 128 x 16 BF16 A matrix of the bias step
+constexpr uint32_t ONES_BYTES = 128 * 16 * 2;
+constexpr uint32_t OFF_BAR = OFF_ONES + ONES_BYTES;  // 1 weights + SLOTS mma + SLOTS epi
 constexpr uint32_t OFF_SLOT = OFF_BAR + 8 * (1 + 2 * SLOTS);
 // fallback queue: indices of this CTA's particles outside the training
 // domain (-1 until written), then [0] the queue tail, [1] the number of
@@ -71,12 +78,12 @@ constexpr uint32_t OFF_FBC = OFF_FBQ + FBQ_CAP * 8;
 constexpr uint32_t SMEM_BYTES = (OFF_FBC + 8 + 127) / 128 * 128;
 static_assert(SMEM_BYTES <= 227 * 1024, "shared memory budget");
 static_assert(SMEM_BYTES > 114 * 1024, "one CTA per SM (it owns all tensor memory)");
-// Tensor memory (columns): slot s holds its FP32 accumulator at 256 s and its
-// BF16 activations (the next MMA's A operand, 2 per column) at 256 s + 128;
-// the bias step's constant A matrix sits at 192.
+// Tensor memory (columns): slot s's FP32 accumulator at 128 s; the BF16
+// activations (the next MMA's A operand, 2 per column) of slots 0 and 1 at
+// 384 + 64 s. Slot 2 keeps its activations in shared memory.
 constexpr uint32_t TMEM_COLS = 512;
-constexpr uint32_t TM_SLOT = 256, TM_ACT = 128, TM_ONES = 192;
-static_assert(TM_SLOT * (SLOTS - 1) + TM_ACT + 64 <= TMEM_COLS && TM_ONES + 8 <= TM_SLOT,
+constexpr uint32_t TM_ACC = 128, TM_ACT0 = 384;
+static_assert(TM_ACC * SLOTS <= TM_ACT0 && TM_ACT0 + 64 * TM_SLOTS <= TMEM_COLS,
               "tensor memory budget");
 
 // Two hidden pre-activations (FP32 accumulators r0, r1, bias included) ->
@@ -108,6 +115,145 @@ BL_DEV void gelu_chunk(const uint32_t (&r)[16], uint32_t t_act, int f0) {
   tc::tmem_st8(t_act + (uint32_t)(f0 / 2), gelu2_pair(r[0], r[1]), gelu2_pair(r[2], r[3]),
                gelu2_pair(r[4], r[5]), gelu2_pair(r[6], r[7]), gelu2_pair(r[8], r[9]),
                gelu2_pair(r[10], r[11]), gelu2_pair(r[12], r[13]), gelu2_pair(r[14], r[15]));
+}
+
+// The same 16 columns written as two 16-byte K chunks of the row in the
+// shared-memory activation buffer (row base `row`, K chunks 128 bytes apart).
+BL_DEV void gelu_chunk_smem(const uint32_t (&r)[16], uint32_t row, int f0) {
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const uint32_t a = gelu2_pair(r[8 * q + 0], r[8 * q + 1]);
+    const uint32_t b = gelu2_pair(r[8 * q + 2], r[8 * q + 3]);
+    const uint32_t d = gelu2_pair(r[8 * q + 4], r[8 * q + 5]);
+    const uint32_t e = gelu2_pair(r[8 * q + 6], r[8 * q + 7]);
+    tc::st_shared_v4(row + (uint32_t)(f0 / 8 + q) * 128, a, b, d, e);
+  }
+}
+
+// Epilogue warps of one slot: activations in tensor memory (TM) or in the
+// shared-memory buffer (the slot the MMA reads with both operands in shared
+// memory).
+template <bool TM>
+BL_DEV void epilogue(Soa<float> &z, int64_t n, int64_t ntiles, const MlpNormF &nrm,
+                     unsigned *err, const MlpDomain &dom, long long *fbq, int *fbc,
+                     uint32_t sbase, uint32_t tmem, uint32_t bar_w, int warp, int lane) {
+    const int wg = warp >> 2, wq = warp & 3;
+    const int slot = wg / WG_PER_SLOT, h = wg % WG_PER_SLOT;
+    const bool io = (h == 0);  // this warpgroup loads inputs and stores outputs
+    const int m = wq * 32 + lane;  // this thread's particle row within a tile
+    const uint32_t t_lane = tmem + ((uint32_t)(wq * 32) << 16);
+    const uint32_t t_acc = t_lane + TM_ACC * slot;
+    const uint32_t t_act = t_lane + TM_ACT0 + 64 * slot;  // slots in tensor memory
+    const uint32_t act = sbase + OFF_ACT;                 // the slot in shared memory
+    const uint32_t row_in = act + (uint32_t)((m >> 3) * 256 + (m & 7) * 16);    // K = 16 layout
+    const uint32_t row_h = act + (uint32_t)((m >> 3) * 2048 + (m & 7) * 16);    // K = 128 layout
+    const uint32_t my_mma = bar_w + 8 * (1 + slot), my_epi = bar_w + 8 * (1 + SLOTS + slot);
+    bool ok = __all_sync(0xffffffffu, tc::mbar_wait(bar_w, 0, BL_DEVERR_TMA_TIMEOUT, err));
+    uint32_t ph = 0;
+    auto done = [&]() {  // hand the activations and the accumulator to the MMA warp
+      if (TM) tc::tmem_st_wait();
+      else tc::fence_proxy_async();
+      tc::fence_before();
+      mbar_arrive(my_epi);
+    };
+    auto wait_mma = [&]() {
+      ok = ok && __all_sync(0xffffffffu, tc::mbar_wait(my_mma, ph, BL_DEVERR_MMA_TIMEOUT, err));
+      ph ^= 1;
+      tc::fence_after();
+    };
+    const int64_t tstride = (int64_t)gridDim.x * SLOTS;
+    int64_t tile = (int64_t)blockIdx.x * SLOTS + slot;
+    float xin[6];
+    {
+      const int64_t p = tile * 128 + m;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) xin[c] = (io && tile < ntiles && p < n) ? z.c[c][p] : 0.0f;
+    }
+    for (; ok && tile < ntiles; tile += tstride) {
+      const int64_t p = tile * 128 + m;
+      const bool valid = p < n;
+      // outside the training-input box: not mapped, but pushed by the plain
+      // pusher (a NaN compares false and is mapped, so it stays visible)
+      bool outside = false;
+      if (dom.fb_list) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) outside |= (xin[c] < dom.lo[c]) | (xin[c] > dom.hi[c]);
+        if (io && valid && outside) {
+          // to this CTA's fallback warp, or, past its queue, to the global
+          // list for the separate list-mode pusher
+          const int k = dom.fused ? atomicAdd(&fbc[0], 1) : FBQ_CAP;
+          if (k < FBQ_CAP) {
+            reinterpret_cast<volatile long long *>(fbq)[k] = p;
+          } else {
+            const unsigned long long g = atomicAdd(dom.fb_count, 1ull);
+            if ((int64_t)g < dom.fb_cap) dom.fb_list[g] = p;
+            else outside = false;  // list full (cannot happen with capacity n): keep the map
+          }
+        }
+      }
+      if (io) {  // normalised input row (K = 16, see input_row)
+        float xn[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+          xn[c] = df_normalise(xin[c], nrm.mu_in[c][0], nrm.mu_in[c][1], nrm.inv_sd_in[c][0],
+                               nrm.inv_sd_in[c][1]);
+        uint32_t w[8];
+        input_row(xn, w);
+        if (TM) {
+          tc::tmem_st8(t_act, w[0], w[1], w[2], w[3], w[4], w[5], w[6], w[7]);
+        } else {
+          tc::st_shared_v4(row_in, w[0], w[1], w[2], w[3]);
+          tc::st_shared_v4(row_in + 128, w[4], w[5], w[6], w[7]);
+        }
+      }
+      done();  // layer 0 may start
+      if (io) {  // prefetch this slot's next tile while the current one is in the network
+        const int64_t tn = tile + tstride, pn = tn * 128 + m;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) xin[c] = (tn < ntiles && pn < n) ? z.c[c][pn] : 0.0f;
+      }
+#pragma unroll 1
+      for (int l = 0; l < 4; ++l) {
+        wait_mma();
+        if (!ok) break;
+        // this warpgroup's FEAT_WG features in chunks of CHUNK columns; the
+        // next chunk's load is in flight while the current one is computed
+        const int f_base = h * FEAT_WG;
+        uint32_t ra[CHUNK], rb[CHUNK];
+        tc::tmem_ld(t_acc + f_base, ra);
+        tc::tmem_ld_wait_regs(ra);
+#pragma unroll
+        for (int c = 0; c < FEAT_WG / CHUNK; c += 2) {
+          const int f = f_base + c * CHUNK;
+          tc::tmem_ld(t_acc + f + CHUNK, rb);
+          if (TM) gelu_chunk(ra, t_act, f);
+          else gelu_chunk_smem(ra, row_h, f);
+          tc::tmem_ld_wait_regs(rb);
+          if (c + 2 < FEAT_WG / CHUNK) tc::tmem_ld(t_acc + f + 2 * CHUNK, ra);
+          if (TM) gelu_chunk(rb, t_act, f + CHUNK);
+          else gelu_chunk_smem(rb, row_h, f + CHUNK);
+          if (c + 2 < FEAT_WG / CHUNK) tc::tmem_ld_wait_regs(ra);
+        }
+        done();  // layer l+1 may read these activations and overwrite the accumulator
+      }
+      if (!ok) break;
+      wait_mma();  // output layer complete
+      if (!ok) break;
+      if (!io) continue;
+      uint32_t r[8];
+      tc::tmem_ld8(t_acc, r);
+      tc::tmem_ld_wait();
+      if (valid && !outside) {  // particles outside the domain are the pushers'
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+          z.c[c][p] = df_affine(__uint_as_float(r[c]), nrm.sd_out[c][0], nrm.sd_out[c][1],
+                                nrm.mu_out[c][0], nrm.mu_out[c][1]);
+      }
+    }
+    // this warp has queued all its fallback particles
+    __syncwarp();
+    __threadfence_block();
+    if (lane == 0) atomicAdd(&fbc[1], 1);
 }
 
 // Registers: the 4 sub-partitions of the SM each hold a quarter of the 64K
@@ -145,21 +291,15 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
     fbc[0] = 0;
     fbc[1] = 0;
   }
+  // constant A operand of the bias step: rows of (1, 1, 0, ..., 0), K-major
+  // core matrices (8 rows x 16 bytes, K chunks 128 bytes apart, row groups
+  // 256 bytes apart)
+  init_ones(smem, OFF_ONES, tid, THREADS);
+  tc::fence_proxy_async();
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = *tslot;
-  // constant A operand of the bias step, in tensor memory: every row
-  // (1, 1, 0, ..., 0) over K = 16, i.e. one packed BF16 pair (1, 1) and seven
-  // zero columns; written by the four warps of the first warpgroup
-  if (warp < 4) {
-    tc::tmem_st8(tmem + ((uint32_t)(warp * 32) << 16) + TM_ONES, tc::pack_bf16x2(1.0f, 1.0f), 0u,
-                 0u, 0u, 0u, 0u, 0u, 0u);
-    tc::tmem_st_wait();
-  }
-  tc::fence_before();
-  __syncthreads();
-  tc::fence_after();
   if (tid == 0) load_weights(sbase, img, bar_w);
 
   if (warp == MMA_WARP) {
@@ -180,8 +320,12 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
       // bias blocks B1..B4 at MLP_IMG_BH (the descriptor address is in 16 B units)
       const uint64_t d_w1 = tc::sdesc(sbase + OFF_W1, 128, 2048);
       const uint64_t d_b1 = tc::sdesc(sbase + OFF_B1, 128, 256);
-      // tensor-memory A operands: a K step of 16 BF16 is 8 columns
-      const uint32_t t_ones = tmem + TM_ONES;
+      // A operands: the bias step's constant matrix and slot 2's activations
+      // in shared memory (K = 16 layout for the input, K = 128 after); slots
+      // 0 and 1 read theirs from tensor memory, 8 columns per K step of 16
+      const uint64_t d_ones = tc::sdesc(sbase + OFF_ONES, 128, 256);
+      const uint64_t d_in0 = tc::sdesc(sbase + OFF_ACT, 128, 256);
+      const uint64_t d_act0 = tc::sdesc(sbase + OFF_ACT, 128, 2048);
       for (int64_t t0 = (int64_t)blockIdx.x * SLOTS; ok && t0 < ntiles;
            t0 += (int64_t)gridDim.x * SLOTS) {
         const int64_t live = ntiles - t0;  // slots s < live hold a tile in this pass
@@ -195,17 +339,21 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
               ph ^= 1u << s_;
               if (ok) {
                 tc::fence_after();
-                const uint32_t acc = tmem + TM_SLOT * s_;
-                const uint32_t act = acc + TM_ACT;
+                const uint32_t acc = tmem + TM_ACC * s_;
+                const uint32_t act = tmem + TM_ACT0 + 64 * s_;
                 if (l == 0) {
-                  tc::mma_ts(acc, act, d_w0, ID_H, 0);
+                  if (s_ < TM_SLOTS) tc::mma_ts(acc, act, d_w0, ID_H, 0);
+                  else tc::mma_ss(acc, d_in0, d_w0, ID_H, 0);
                 } else {
                   const uint64_t dw = d_w1 + (uint64_t)((l - 1) * (MLP_IMG_WH >> 4));
                   const uint64_t db = d_b1 + (uint64_t)((l - 1) * (MLP_IMG_BH >> 4));
                   const uint32_t id = (l < 4) ? ID_H : ID_O;
 #pragma unroll
-                  for (int j = 0; j < 8; ++j) tc::mma_ts(acc, act + 8 * j, dw + 16 * j, id, j > 0);
-                  tc::mma_ts(acc, t_ones, db, id, 1);
+                  for (int j = 0; j < 8; ++j) {
+                    if (s_ < TM_SLOTS) tc::mma_ts(acc, act + 8 * j, dw + 16 * j, id, j > 0);
+                    else tc::mma_ss(acc, d_act0 + 16 * j, dw + 16 * j, id, j > 0);
+                  }
+                  tc::mma_ss(acc, d_ones, db, id, 1);
                 }
                 tc::mma_commit(bar_w + 8 * (1 + s_));
               }
@@ -261,111 +409,11 @@ mlp_forward_kernel(Soa<float> z, int64_t n, int64_t ntiles, const uint8_t *__res
     }
   } else {
     // ------------------------------------------------------ epilogue warps
-    const int wg = warp >> 2, wq = warp & 3;
-    const int slot = wg / WG_PER_SLOT, h = wg % WG_PER_SLOT;
-    const bool io = (h == 0);  // this warpgroup loads inputs and stores outputs
-    const int m = wq * 32 + lane;  // this thread's particle row within a tile
-    const uint32_t t_acc = tmem + ((uint32_t)(wq * 32) << 16) + TM_SLOT * slot;
-    const uint32_t t_act = t_acc + TM_ACT;  // this warp's lanes of the slot's activations
-    const uint32_t my_mma = bar_w + 8 * (1 + slot), my_epi = bar_w + 8 * (1 + SLOTS + slot);
-    bool ok = __all_sync(0xffffffffu, tc::mbar_wait(bar_w, 0, BL_DEVERR_TMA_TIMEOUT, err));
-    uint32_t ph = 0;
-    auto done = [&]() {  // hand the activations and the accumulator to the MMA warp
-      tc::tmem_st_wait();
-      tc::fence_before();
-      mbar_arrive(my_epi);
-    };
-    auto wait_mma = [&]() {
-      ok = ok && __all_sync(0xffffffffu, tc::mbar_wait(my_mma, ph, BL_DEVERR_MMA_TIMEOUT, err));
-      ph ^= 1;
-      tc::fence_after();
-    };
-    const int64_t tstride = (int64_t)gridDim.x * SLOTS;
-    int64_t tile = (int64_t)blockIdx.x * SLOTS + slot;
-    float xin[6];
-    {
-      const int64_t p = tile * 128 + m;
-#pragma unroll
-      for (int c = 0; c < 6; ++c) xin[c] = (io && tile < ntiles && p < n) ? z.c[c][p] : 0.0f;
-    }
-    for (; ok && tile < ntiles; tile += tstride) {
-      const int64_t p = tile * 128 + m;
-      const bool valid = p < n;
-      // outside the training-input box: not mapped, but pushed by the plain
-      // pusher (a NaN compares false and is mapped, so it stays visible)
-      bool outside = false;
-      if (dom.fb_list) {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) outside |= (xin[c] < dom.lo[c]) | (xin[c] > dom.hi[c]);
-        if (io && valid && outside) {
-          // to this CTA's fallback warp, or, past its queue, to the global
-          // list for the separate list-mode pusher
-          const int k = dom.fused ? atomicAdd(&fbc[0], 1) : FBQ_CAP;
-          if (k < FBQ_CAP) {
-            reinterpret_cast<volatile long long *>(fbq)[k] = p;
-          } else {
-            const unsigned long long g = atomicAdd(dom.fb_count, 1ull);
-            if ((int64_t)g < dom.fb_cap) dom.fb_list[g] = p;
-            else outside = false;  // list full (cannot happen with capacity n): keep the map
-          }
-        }
-      }
-      if (io) {  // normalised input row (K = 16, see input_row)
-        float xn[6];
-#pragma unroll
-        for (int c = 0; c < 6; ++c)
-          xn[c] = df_normalise(xin[c], nrm.mu_in[c][0], nrm.mu_in[c][1], nrm.inv_sd_in[c][0],
-                               nrm.inv_sd_in[c][1]);
-        uint32_t w[8];
-        input_row(xn, w);
-        tc::tmem_st8(t_act, w[0], w[1], w[2], w[3], w[4], w[5], w[6], w[7]);
-      }
-      done();  // layer 0 may start
-      if (io) {  // prefetch this slot's next tile while the current one is in the network
-        const int64_t tn = tile + tstride, pn = tn * 128 + m;
-#pragma unroll
-        for (int c = 0; c < 6; ++c) xin[c] = (tn < ntiles && pn < n) ? z.c[c][pn] : 0.0f;
-      }
-#pragma unroll 1
-      for (int l = 0; l < 4; ++l) {
-        wait_mma();
-        if (!ok) break;
-        // this warpgroup's FEAT_WG features in chunks of CHUNK columns; the
-        // next chunk's load is in flight while the current one is computed
-        const int f_base = h * FEAT_WG;
-        uint32_t ra[CHUNK], rb[CHUNK];
-        tc::tmem_ld(t_acc + f_base, ra);
-        tc::tmem_ld_wait_regs(ra);
-#pragma unroll
-        for (int c = 0; c < FEAT_WG / CHUNK; c += 2) {
-          const int f = f_base + c * CHUNK;
-          tc::tmem_ld(t_acc + f + CHUNK, rb);
-          gelu_chunk(ra, t_act, f);
-          tc::tmem_ld_wait_regs(rb);
-          if (c + 2 < FEAT_WG / CHUNK) tc::tmem_ld(t_acc + f + 2 * CHUNK, ra);
-          gelu_chunk(rb, t_act, f + CHUNK);
-          if (c + 2 < FEAT_WG / CHUNK) tc::tmem_ld_wait_regs(ra);
-        }
-        done();  // layer l+1 may read these activations and overwrite the accumulator
-      }
-      if (!ok) break;
-      wait_mma();  // output layer complete
-      if (!ok) break;
-      if (!io) continue;
-      uint32_t r[8];
-      tc::tmem_ld8(t_acc, r);
-      tc::tmem_ld_wait();
-      if (valid && !outside) {  // particles outside the domain are the pushers'
-#pragma unroll
-        for (int c = 0; c < 6; ++c)
-          z.c[c][p] = df_affine(__uint_as_float(r[c]), nrm.sd_out[c][0], nrm.sd_out[c][1],
-                                nrm.mu_out[c][0], nrm.mu_out[c][1]);
-      }
-    }
-    // this warp has queued all its fallback particles
-    __syncwarp();
-    __threadfence_block();
-    if (lane == 0) atomicAdd(&fbc[1], 1);
+    const int slot = (warp >> 2) / WG_PER_SLOT;
+    if (slot < TM_SLOTS)
+      epilogue<true>(z, n, ntiles, nrm, err, dom, fbq, fbc, sbase, tmem, bar_w, warp, lane);
+    else
+      epilogue<false>(z, n, ntiles, nrm, err, dom, fbq, fbc, sbase, tmem, bar_w, warp, lane);
   }
   tc::fence_before();
   __syncthreads();
