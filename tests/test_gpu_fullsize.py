@@ -44,7 +44,9 @@ def test_fullsize_pusher_beamline(full_bunch):
     for a, w in zip(got, zo):
         err = np.max(np.abs(a[idx] - w)) / np.std(w)
         print("pusher beamline, sampled particles: max err / rms %.3e" % err)
-        assert err < 3e-3  # FP32 deviation-form RK4 over 8 x 400 steps
+        # FP32 deviation-form RK4: the per-stage phase error budget of the
+        # 400-step test (1.3e-4 rms) over 8 stages, 1e-3 (measured 4.8e-4)
+        assert err < 1.5e-3
     # moments of the whole final bunch: the library's reduction against the
     # oracle's moments of the same FP32 particles (1e-10), and bl_track's last
     # snapshot (entry reduction propagated in FP64 through the last segment)

@@ -155,7 +155,14 @@ def test_pusher_fp32_400_steps():
     rel = {k: abs(dg[k] / dw[k] - 1) for k in dw}
     print("fp32 pusher per-coordinate max err / rms:", errs, "moments:", rel)
     assert max(rel.values()) < 1e-5
-    assert max(errs) < 1e-3
+    # Per particle the FP32 error is a betatron phase error: each step turns
+    # the particle by mu/N ~ 0.4 rad (mu up to ~160 rad over the stage), and
+    # FP32 evaluation of that turn (plus the rounding of the wake phase
+    # k_p t) is off by ~1e-7 relative, i.e. ~8e-8 rad per step. Over 400
+    # steps that is at most ~3e-5 rad if every step erred the same way, and a
+    # particle of betatron amplitude <= 4 rms then moves by <= 1.3e-4 rms
+    # (measured: 1.1e-4). Hence 3e-4; the moments are held to 1e-5.
+    assert max(errs) < 3e-4
 
 
 def test_track_config1_fp64_moments_every_element():
@@ -217,7 +224,7 @@ def test_track_plasma_lens_section(dtype):
     for e, (want, gr) in enumerate(snaps):
         _cmp_moments(mom[e][0], want, tol)
     got = from_bunch(b)
-    ptol = 1e-10 if dtype == "f64" else 1e-3  # FP32: 200-step stage, as the pusher test
+    ptol = 1e-10 if dtype == "f64" else 3e-4  # FP32: phase error budget as the pusher test
     for a, w in zip(got, zo):
         assert np.max(np.abs(a - w)) <= ptol * np.std(w)
 
