@@ -36,11 +36,14 @@ N_STAGES = 8
 STEPS_PER_STAGE = 400
 FLOP_PER_PARTICLE_STAGE = 2 * (6 * 128 + 3 * 128 * 128 + 128 * 6)  # 101,376
 SEG_BYTES_PER_PARTICLE = 48
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one
-# mlp_forward_kernel launch on 8,388,608 particles in one ncu capture of the
-# current kernel (201.6 MB + 139.8 MB), scaled per particle to the launch size
-MLP_DRAM_BYTES_PER_PARTICLE = (201.568768e6 + 139.784192e6) / 8388608
-MLP_DRAM_BASIS = "ncu dram bytes of one launch on 2^23 particles, scaled by the particle count"
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch on
+# 8,388,608 particles in one ncu capture of each current kernel, scaled per
+# particle to the launch size: mlp_forward_kernel 201.6 MB + 139.7 MB,
+# seg_f32_kernel<apply, moments> 201.6 MB + 140.3 MB (the writes still in L2
+# when a kernel ends are not counted)
+MLP_DRAM_BYTES_PER_PARTICLE = (201.640448e6 + 139.659520e6) / 8388608
+SEG_DRAM_BYTES_PER_PARTICLE = (201.641728e6 + 140.295680e6) / 8388608
+DRAM_BASIS = "ncu dram bytes of one launch on 2^23 particles, scaled by the particle count"
 # algorithmic flop per particle-stage of a whole gradient: the forward
 # surrogate pass plus the VJP (forward recomputation and reverse sweep)
 ADJOINT_FLOP_PER_PARTICLE_STAGE = 3 * FLOP_PER_PARTICLE_STAGE
@@ -691,11 +694,12 @@ def main():
         "moment_rel_err_vs_pusher": moment_err,
         "roofline": {"bound": "tensor", "achieved": mlp_tflops, "peak": bf16_peak,
                      "unit": "TFLOP/s", "frac": mlp_tflops / bf16_peak,
-                     "traffic": MLP_DRAM_BYTES_PER_PARTICLE * n, "traffic_basis": MLP_DRAM_BASIS,
+                     "traffic": MLP_DRAM_BYTES_PER_PARTICLE * n, "traffic_basis": DRAM_BASIS,
                      "kernel": "mlp_forward_kernel", "peak_source": peak_src + " bf16 burst",
                      "ms_per_launch": mlp_ms},
         "roofline_segment": {"bound": "hbm", "achieved": seg_gbs, "peak": hbm_peak, "unit": "GB/s",
                              "frac": seg_gbs / hbm_peak,
+                             "traffic": SEG_DRAM_BYTES_PER_PARTICLE * n, "traffic_basis": DRAM_BASIS,
                              "kernel": "seg_f32_kernel<apply, moments> + moments_finalize_kernel "
                                        "(the segment pass of every stage of the step)",
                              "bytes_per_particle": SEG_BYTES_PER_PARTICLE,
