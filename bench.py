@@ -638,6 +638,22 @@ def main():
     fin_d, fin_e = np.asarray(m_sur)[-1][0], m_e2e[-1][0]
     e2e_mom_diff = (float(np.max(np.abs(fin_e[7:] - fin_d[7:])) / np.abs(fin_d[7:]).max())
                     if world == 1 else None)
+    # the host link itself: the whole bunch copied in, then out, alone
+    dev_tmp = [torch.empty_like(c) for c in bunch.coords]
+    for d_, h_ in zip(dev_tmp, host_pinned):
+        d_.copy_(h_, non_blocking=True)
+    torch.cuda.synchronize()
+    ev3 = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev3[0].record(stream)
+    for d_, h_ in zip(dev_tmp, host_pinned):
+        d_.copy_(h_, non_blocking=True)
+    ev3[1].record(stream)
+    for h_, d_ in zip(out_host, dev_tmp):
+        h_.copy_(d_, non_blocking=True)
+    ev3[2].record(stream)
+    torch.cuda.synchronize()
+    h2d_ms, d2h_ms = ev3[0].elapsed_time(ev3[1]), ev3[1].elapsed_time(ev3[2])
+    del dev_tmp
     nchunks = -(-n // chunk)
     n_red = bl.lib().bl_track_num_reductions(lat_sur.handle)
     n_regions = 2 * nchunks + 1 if nchunks > 1 else 1  # head and tail per chunk, middle once
@@ -712,7 +728,12 @@ def main():
                 "call": "bl_track_host, page-locked host buffers, %d chunks of 2^21 particles: "
                         "copies in overlap the first stage, copies out the last; the bunch "
                         "stays on the device in between" % nchunks,
-                "final_second_moments_max_rel_diff_vs_device": e2e_mom_diff},
+                "final_second_moments_max_rel_diff_vs_device": e2e_mom_diff,
+                "link": {"h2d_ms": h2d_ms, "d2h_ms": d2h_ms,
+                         "h2d_gbs": 6 * 4 * n / (h2d_ms * 1e-3) / 1e9,
+                         "d2h_gbs": 6 * 4 * n / (d2h_ms * 1e-3) / 1e9,
+                         "timing": "the bunch copied alone, page-locked host <-> device, "
+                                   "CUDA events"}},
         "gpu_launches": launches_per_step * args.steps,
         **extras,
         "clocks": clk,
