@@ -70,7 +70,7 @@ def load_peaks():
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--steps", type=int, default=50)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--particles", type=int, default=N_PARTICLES)
@@ -136,6 +136,29 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ reference arm
+def host_cpu():
+    """Model name and logical CPU count of this host (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"model": model, "logical_cpus": os.cpu_count()}
+
+
 def cpu_oracle_rate(sample, nets=None, seconds_cap=30.0):
     """Oracle (FP64 numpy) surrogate beamline on a bounded sample; returns
     particle-stages/s, the thread count numpy/BLAS may use and a description."""
@@ -190,7 +213,7 @@ def run_reference(args):
             "config": {"workload": "8-stage surrogate beamline, FP64 CPU oracle sample",
                        "particles_per_step": sample, "stages": N_STAGES},
             "cpu_baseline": {"value": value, "unit": "particle-stages/s", "cores": cores,
-                             "kind": "oracle", "sample": desc},
+                             "kind": "oracle", "sample": desc, "host": host_cpu()},
             "e2e": {"value": value, "unit": "particle-stages/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -678,6 +701,7 @@ def main():
                                        s.mu_in, s.sd_in, s.mu_out, s.sd_out))
         rate, cores, dt = cpu_oracle_rate(args.cpu_sample, nets)
         cpu = {"value": rate, "unit": "particle-stages/s", "cores": cores, "kind": "oracle",
+               "host": host_cpu(),
                "sample": "FP64 numpy oracle of the trained 8-stage surrogate beamline with "
                          "moments after every element, %d particles (%.1f s)" % (args.cpu_sample, dt)}
         # the plain method on the host: the oracle's FP64 RK4 stage push
