@@ -1,4 +1,5 @@
 // C ABI: stage surrogates (create, inference, training, loss, parameters).
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -52,11 +53,19 @@ void free_surrogate(bl_surrogate_s *s) {
 
 std::atomic<bool> g_train_simt{false};
 
-// Partial gradients and losses of one minibatch, from the tensor-core kernel
+// Samples per gradient launch: a larger minibatch is processed in chunks of
+// this size, each chunk's partial rows added to one running FP64 row, so the
+// partial rows (205 KB per 128-sample tile) and the tensor-core kernel's
+// activation scratch (100 KB per tile) stay near 210 MB and 105 MB however
+// large the batch (2^24 samples would otherwise need 27 GB and 13 GB).
+constexpr int64_t TRAIN_CHUNK = (int64_t)1 << 17;
+
+// Partial gradients and losses of `batch` samples starting at sample s0
+// (scaled as a mean over scale_count samples), from the tensor-core kernel
 // (default) or the SIMT FP32 kernel; *nb_out = the number of partial rows.
-bl_status train_grad(bl_surrogate *s, const float *in, const float *out, int64_t ld,
-                     const int64_t *idx, int64_t batch, float **part_out, double **lp_out,
-                     int *nb_out, cudaStream_t st) {
+bl_status train_grad_part(bl_surrogate *s, const float *in, const float *out, int64_t ld,
+                          const int64_t *idx, int64_t s0, int64_t batch, int64_t scale_count,
+                          float **part_out, double **lp_out, int *nb_out, cudaStream_t st) {
   DevCtx *ctx = nullptr;
   BL_TRY(current_ctx(&ctx));
   const bool simt = g_train_simt.load();
@@ -64,10 +73,13 @@ bl_status train_grad(bl_surrogate *s, const float *in, const float *out, int64_t
   void *part = nullptr, *lp = nullptr;
   BL_TRY(ws_get(st, WS_TRAIN, (size_t)nb * MLP_PSTRIDE * sizeof(float), &part));
   BL_TRY(ws_get(st, WS_LOSS, (size_t)nb * sizeof(double), &lp));
+  // the chunk's samples: columns s0.. of in/out, or entries s0.. of idx
+  const float *ci = idx ? in : in + s0, *co = idx ? out : out + s0;
+  const int64_t *cx = idx ? idx + s0 : nullptr;
   if (simt) {
     int nb2 = 0;
-    BL_CUDA(launch_mlp_grad(in, out, ld, idx, batch, s->wt, s->wn, s->nrm, (float *)part,
-                            (double *)lp, &nb2, st));
+    BL_CUDA(launch_mlp_grad(ci, co, ld, cx, batch, s->wt, s->wn, s->nrm, (float *)part,
+                            (double *)lp, &nb2, st, scale_count));
   } else {
     if (!ctx->train_tc_configured) {
       BL_CUDA(mlp_train_tc_configure());
@@ -75,12 +87,43 @@ bl_status train_grad(bl_surrogate *s, const float *in, const float *out, int64_t
     }
     void *scratch = nullptr;
     BL_TRY(ws_get(st, WS_TRAIN_SCRATCH, mlp_train_tc_scratch_bytes(batch), &scratch));
-    BL_CUDA(launch_mlp_grad_tc(in, out, ld, idx, batch, s->img, s->bias, s->nrm, (float *)part,
-                               (double *)lp, (uint8_t *)scratch, ctx->num_sms, ctx->err_word, st));
+    BL_CUDA(launch_mlp_grad_tc(ci, co, ld, cx, batch, s->img, s->bias, s->nrm, (float *)part,
+                               (double *)lp, (uint8_t *)scratch, ctx->num_sms, ctx->err_word, st,
+                               scale_count));
   }
   *part_out = (float *)part;
   *lp_out = (double *)lp;
   *nb_out = nb;
+  return BL_OK;
+}
+
+// Partial gradients and losses of one minibatch: *nb_out partial rows (one
+// running row when the batch was processed in chunks).
+bl_status train_grad(bl_surrogate *s, const float *in, const float *out, int64_t ld,
+                     const int64_t *idx, int64_t batch, float **part_out, double **lp_out,
+                     int *nb_out, cudaStream_t st) {
+  if (batch <= TRAIN_CHUNK)
+    return train_grad_part(s, in, out, ld, idx, 0, batch, batch, part_out, lp_out, nb_out, st);
+  // [FP64 running row | FP64 running loss | the final FP32 row]
+  const size_t acc_bytes = (MLP_PSTRIDE + 1) * sizeof(double);
+  void *acc = nullptr;
+  BL_TRY(ws_get(st, WS_TRAIN_ACC, acc_bytes + MLP_PSTRIDE * sizeof(float), &acc));
+  double *acc_row = (double *)acc;
+  double *acc_loss = acc_row + MLP_PSTRIDE;
+  float *row = (float *)((uint8_t *)acc + acc_bytes);
+  BL_CUDA(cudaMemsetAsync(acc, 0, acc_bytes, st));
+  for (int64_t s0 = 0; s0 < batch; s0 += TRAIN_CHUNK) {
+    float *part = nullptr;
+    double *lp = nullptr;
+    int nb = 0;
+    BL_TRY(train_grad_part(s, in, out, ld, idx, s0, std::min(TRAIN_CHUNK, batch - s0), batch,
+                           &part, &lp, &nb, st));
+    BL_CUDA(launch_mlp_rows_accumulate(part, nb, lp, acc_row, acc_loss,
+                                       s0 + TRAIN_CHUNK >= batch ? row : nullptr, st));
+  }
+  *part_out = row;
+  *lp_out = acc_loss;
+  *nb_out = 1;
   return BL_OK;
 }
 

@@ -157,10 +157,19 @@ int mlp_grad_blocks(int64_t count);
 // Minibatch MSE gradient with the SIMT kernels (mlp_train.cu): in/out are
 // coordinate-major [6][ld] FP32; partials: mlp_grad_blocks(batch) rows of
 // MLP_PSTRIDE floats; loss_partials: one double per block.
+// scale_count (0: batch) is the sample count the MSE is averaged over, so a
+// large minibatch can be processed in chunks with the whole batch's scale.
 cudaError_t launch_mlp_grad(const float *in, const float *out, int64_t ld, const int64_t *idx,
                             int64_t batch, const float *wt, const float *wn, const MlpNorm &nrm,
                             float *partials, double *loss_partials, int *nblocks_out,
-                            cudaStream_t st);
+                            cudaStream_t st, int64_t scale_count = 0);
+// acc[i] += rows[b][i] (i < MLP_NPARAM) and *acc_loss += loss_rows[b] for
+// b = 0 .. nrows-1, in FP64: the partial rows of one chunk of a minibatch
+// added to the running sums. With `row_out`, the sums are then also written
+// to it as one FP32 partial row.
+cudaError_t launch_mlp_rows_accumulate(const float *rows, int nrows, const double *loss_rows,
+                                       double *acc, double *acc_loss, float *row_out,
+                                       cudaStream_t st);
 // Sum partial gradients; if step > 0 apply Adam with bias correction for
 // step t = step. grad_out (device, NPARAM) and loss_out (device) optional.
 // Minibatch MSE gradient on the tensor cores (mlp_train_tc.cu): one
@@ -173,7 +182,8 @@ cudaError_t mlp_train_tc_configure();
 cudaError_t launch_mlp_grad_tc(const float *in, const float *out, int64_t ld, const int64_t *idx,
                                int64_t batch, const uint8_t *img, const float *bias,
                                const MlpNorm &nrm, float *partials, double *loss_partials,
-                               uint8_t *scratch, int num_sms, unsigned *err, cudaStream_t st);
+                               uint8_t *scratch, int num_sms, unsigned *err, cudaStream_t st,
+                               int64_t scale_count = 0);
 // Which gradient kernel the training entry points use: false = tensor cores
 // (default), true = the SIMT FP32 kernel (bl_debug_train_kernel).
 bool mlp_train_use_simt();

@@ -288,7 +288,7 @@ __global__ void loss_finalize_kernel(const double *__restrict__ lp, int nblocks,
 template <int MODE>
 cudaError_t launch_grad_mode(Soa<float> zin, Soa<float> zout, const int64_t *idx, int64_t count,
                              const float *wt, const float *wn, const MlpNorm &nrm, float *part,
-                             double *loss_part, cudaStream_t st) {
+                             double *loss_part, cudaStream_t st, int64_t scale_count = 0) {
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(mlp_grad_kernel<MODE>,
@@ -299,7 +299,7 @@ cudaError_t launch_grad_mode(Soa<float> zin, Soa<float> zout, const int64_t *idx
   }
   if (count <= 0) return cudaSuccess;
   const int64_t nb = (count + S - 1) / S;
-  const double inv = 1.0 / (6.0 * (double)count);
+  const double inv = 1.0 / (6.0 * (double)(scale_count > 0 ? scale_count : count));
   mlp_grad_kernel<MODE><<<(unsigned)nb, NT, sizeof(Smem), st>>>(zin, zout, idx, count, wt, wn,
                                                                 nrm, part, loss_part, inv);
   return cudaGetLastError();
@@ -318,10 +318,35 @@ int mlp_grad_blocks(int64_t count) { return (int)((count + S - 1) / S); }
 cudaError_t launch_mlp_grad(const float *in, const float *out, int64_t ld, const int64_t *idx,
                             int64_t batch, const float *wt, const float *wn, const MlpNorm &nrm,
                             float *partials, double *loss_partials, int *nblocks_out,
-                            cudaStream_t st) {
+                            cudaStream_t st, int64_t scale_count) {
   *nblocks_out = mlp_grad_blocks(batch);
   return launch_grad_mode<MODE_TRAIN>(cols6(in, ld), cols6(out, ld), idx, batch, wt, wn, nrm,
-                                      partials, loss_partials, st);
+                                      partials, loss_partials, st, scale_count);
+}
+
+__global__ void __launch_bounds__(256)
+rows_accumulate_kernel(const float *__restrict__ rows, int nrows, const double *__restrict__ lr,
+                       double *__restrict__ acc, double *__restrict__ acc_loss,
+                       float *__restrict__ row_out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    double t = *acc_loss;
+    for (int b = 0; b < nrows; ++b) t += lr[b];
+    *acc_loss = t;
+  }
+  if (i >= MLP_NPARAM) return;
+  double g = acc[i];
+  for (int b = 0; b < nrows; ++b) g += (double)rows[(int64_t)b * MLP_PSTRIDE + i];
+  acc[i] = g;
+  if (row_out) row_out[i] = (float)g;
+}
+
+cudaError_t launch_mlp_rows_accumulate(const float *rows, int nrows, const double *loss_rows,
+                                       double *acc, double *acc_loss, float *row_out,
+                                       cudaStream_t st) {
+  rows_accumulate_kernel<<<(MLP_NPARAM + 255) / 256, 256, 0, st>>>(rows, nrows, loss_rows, acc,
+                                                                   acc_loss, row_out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_mlp_reduce_adam(const float *partials, int nblocks, const double *loss_partials,

@@ -594,7 +594,8 @@ cudaError_t mlp_train_tc_configure() {
 cudaError_t launch_mlp_grad_tc(const float *in, const float *out, int64_t ld, const int64_t *idx,
                                int64_t batch, const uint8_t *img, const float *bias,
                                const MlpNorm &nrm64, float *partials, double *loss_partials,
-                               uint8_t *scratch, int num_sms, unsigned *err, cudaStream_t st) {
+                               uint8_t *scratch, int num_sms, unsigned *err, cudaStream_t st,
+                               int64_t scale_count) {
   if (batch <= 0) return cudaSuccess;
   TrainArgs a{};
   for (int c = 0; c < 6; ++c) {
@@ -610,7 +611,7 @@ cudaError_t launch_mlp_grad_tc(const float *in, const float *out, int64_t ld, co
   a.img = img;
   a.bias = bias;
   a.nrm = norm_pairs(nrm64);
-  a.two_inv_count6 = (float)(2.0 / (6.0 * (double)batch));
+  a.two_inv_count6 = (float)(2.0 / (6.0 * (double)(scale_count > 0 ? scale_count : batch)));
   a.part = partials;
   a.loss_part = loss_partials;
   a.scratch = scratch;

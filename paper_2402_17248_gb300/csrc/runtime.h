@@ -64,7 +64,7 @@ bl_status current_ctx(DevCtx **out);
 enum WsSlot {
   WS_PARTIALS = 0, WS_MOMENTS, WS_NONFINITE, WS_TABLES, WS_MATS, WS_CENTERS, WS_LAMBDA,
   WS_CKPT, WS_CROSS, WS_TRAIN, WS_LOSS, WS_WIDE0, WS_WIDE1, WS_FALLBACK, WS_TRAIN_SCRATCH,
-  WS_HOST_BUF, WS_HOST_RED, WS_WIDE_TRAIN, WS_COUNT
+  WS_HOST_BUF, WS_HOST_RED, WS_WIDE_TRAIN, WS_TRAIN_ACC, WS_COUNT
 };
 struct Workspace {
   void *ptr[WS_COUNT] = {};

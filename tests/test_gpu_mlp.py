@@ -324,3 +324,64 @@ def test_adam_over_many_steps_matches_oracle(tmp_path):
           % (steps, rm, rv, rp))
     assert rm < 1e-6 and rv < 1e-6
     assert rp < 1e-5
+
+
+def _split_grad(sur, din, dout, idx, nA):
+    """Gradient and loss of the whole batch and of its first nA samples and
+    the rest, each from its own bl_surrogate_grad call."""
+    import torch
+    from paper_2402_17248_gb300 import bl
+    out = []
+    parts = [(None, None)]
+    parts.append((0, nA))
+    parts.append((nA, None))
+    for a, b in parts:
+        g = torch.zeros(bl.BL_MLP_NPARAM, device="cuda")
+        loss = torch.zeros(1, device="cuda")
+        if idx is not None:
+            sel = idx if a is None else idx[a:b].contiguous()
+            bl.bl_surrogate_grad(sur, din, dout, g, idx=sel, loss_out=loss)
+            n = sel.numel()
+        else:
+            i_ = din if a is None else din[:, a:b].contiguous()
+            o_ = dout if a is None else dout[:, a:b].contiguous()
+            bl.bl_surrogate_grad(sur, i_, o_, g, loss_out=loss)
+            n = i_.shape[1]
+        torch.cuda.synchronize()
+        out.append((g.double().cpu().numpy(), float(loss.item()), n))
+    return out
+
+
+# a batch just past the 2^17-sample launch chunk (two chunks, the second
+# ragged), gathered through an index vector and read as contiguous columns;
+# and the API's largest batch, 2^24 samples (128 chunks)
+@pytest.mark.parametrize("batch,with_idx", [((1 << 17) + 5003, True),
+                                            ((1 << 17) + 5003, False),
+                                            (1 << 24, False)])
+def test_gradient_large_batch_in_chunks(train_kernel, batch, with_idx):
+    """A minibatch larger than one gradient launch (2^17 samples) is taken in
+    chunks whose partial rows are added to one running row, each chunk
+    scaled as a mean over the whole batch, so the workspace stays bounded.
+    Its gradient and loss are the sample-weighted mean of those of two
+    sub-batches computed by separate calls, to FP32 summation rounding."""
+    import torch
+    from paper_2402_17248_gb300 import bl
+    if train_kernel == "simt" and batch > (1 << 20):
+        pytest.skip("the SIMT kernel is a cross-check at moderate batch sizes")
+    g = torch.Generator(device="cuda").manual_seed(batch % 1000)
+    din = torch.randn(6, batch, device="cuda", generator=g)
+    dout = din + 0.1 * torch.randn(6, batch, device="cuda", generator=g)
+    Ws, bs = mlp_init(WIDTHS, 5)
+    sur = bl.Surrogate(Ws, bs, np.zeros(6), np.ones(6), np.zeros(6), np.ones(6))
+    idx = None
+    if with_idx:
+        idx = torch.randperm(batch, device="cuda", generator=g)
+    nA = (1 << 16) if batch < (1 << 20) else batch // 2
+    (ga, La, n), (g1, L1, n1), (g2, L2, n2) = _split_grad(sur, din, dout, idx, nA)
+    assert n == batch and n1 + n2 == batch
+    want = (n1 * g1 + n2 * g2) / batch
+    rel = np.linalg.norm(ga - want) / np.linalg.norm(want)
+    print("%s batch %d: whole-batch vs split gradient rel diff %.2e, loss %.8e vs %.8e"
+          % (train_kernel, batch, rel, La, (n1 * L1 + n2 * L2) / batch))
+    assert rel < 1e-5
+    assert abs(La / ((n1 * L1 + n2 * L2) / batch) - 1) < 1e-6
