@@ -361,7 +361,10 @@ typedef struct {
  * constants; the loss is the MSE over the normalised targets.
  * loss_out: device float, or NULL; receives the minibatch loss before the
  * update. The step counter t used for bias correction is kept in the
- * surrogate and advanced by one. */
+ * surrogate and advanced by one. 1 <= batch <= 2^24; a batch above 2^17
+ * samples is processed in launches of 2^17 whose partial gradients are
+ * summed in FP64, so the library's work buffers stay near 320 MB however
+ * large the batch (BL_ERR_OOM if they cannot be allocated). */
 bl_status bl_surrogate_train_step(bl_surrogate *s, const float *in, const float *out,
                                   int64_t ld, const int64_t *idx, int64_t batch,
                                   const bl_adam_cfg *cfg, float *loss_out,
