@@ -42,7 +42,7 @@ SEG_BYTES_PER_PARTICLE = 48
 # seg_f32_kernel<apply, moments> 201.6 MB + 140.3 MB (the writes still in L2
 # when a kernel ends are not counted)
 MLP_DRAM_BYTES_PER_PARTICLE = (201.640448e6 + 139.659520e6) / 8388608
-SEG_DRAM_BYTES_PER_PARTICLE = (201.641728e6 + 140.295680e6) / 8388608
+SEG_DRAM_BYTES_PER_PARTICLE = (201.502720e6 + 140.391680e6) / 8388608
 DRAM_BASIS = "ncu dram bytes of one launch on 2^23 particles, scaled by the particle count"
 # algorithmic flop per particle-stage of a whole gradient: the forward
 # surrogate pass plus the VJP (forward recomputation and reverse sweep)

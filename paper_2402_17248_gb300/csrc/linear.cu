@@ -101,13 +101,16 @@ stream_kernel(Soa<T> zin, Soa<T> zout, int64_t n, const int64_t *__restrict__ of
 // per coordinate, completion counted in bytes on an mbarrier): the first
 // STAGES are issued at the start, and each later one by the last warp to
 // release the stage it reuses, so later sub-chunks are in flight while the
-// warps compute and no warp is set aside for the copies. Eight warps in two
-// roles read a stage with vector shared-memory loads, PPT particles per
-// thread: the even warps accumulate sums 0..13 (6 linear sums, 8 products)
+// warps compute and no warp is set aside for the copies. One CTA of eight
+// warps runs per SM, so that each thread has the registers for four
+// particles and its sums without spilling (two CTAs of 128 registers a
+// thread ran 1.9x slower with these sums). The warps, in two roles, read a
+// stage with 16-byte shared-memory loads, PPT particles per thread: the even
+// warps accumulate sums 0..13 (6 linear sums, 8 products)
 // and the non-finite count and write output rows 0..2; the odd warps take
 // sums 14..26 and rows 3..5, with vector stores. The sums stay in per-thread
-// float-float registers across the whole range and are reduced across the
-// block (float-float within a warp, FP64 across warps) only where a bunch or
+// registers across the whole range (biased sums, folded every FOLD_SUBS
+// stages into float-float pairs) and are reduced across the block (float-float within a warp, FP64 across warps) only where a bunch or
 // the range ends, so a CTA pays one block reduction per bunch piece rather
 // than one per few thousand particles. Every wait is bounded; after a
 // timeout the warps keep the same sequence of block barriers without
@@ -115,16 +118,17 @@ stream_kernel(Soa<T> zin, Soa<T> zout, int64_t n, const int64_t *__restrict__ of
 namespace segk {
 constexpr int WARPS = 8;
 constexpr int THREADS = 32 * WARPS;
-constexpr int PPT = 2;                  // particles per thread and pass (two keep the
-                                        // float-float sums within the register budget)
-constexpr int PASS = 128 * PPT;         // particles per pass of the block over a stage
+constexpr int PPT = 4;                  // particles per thread and pass
+constexpr int PASS = (WARPS / 2) * 32 * PPT;  // particles per pass of the block over a stage
 constexpr int PASSES = 4;               // passes per stage
 constexpr int SUB = PASS * PASSES;      // particles per ring stage
 constexpr int STAGES = 4;
 constexpr int MIN_SUB_PER_CTA = 4;      // a unit spans >= 4096 particles: at most as many
                                         // partial slots as the generic kernel's blocks
 static_assert(MIN_SUB_PER_CTA * SUB >= 4096, "unit");
-constexpr int RENORM_SUBS = 2;          // float-float renormalisation period (stages)
+constexpr int FOLD_SUBS = 1;            // stages between folds of the biased sums
+constexpr int FOLD_TERMS = PPT * PASSES * FOLD_SUBS;  // terms a thread adds between folds
+constexpr float BIAS_MUL = 2.0f * FOLD_TERMS;         // bias = BIAS_MUL * (bound of a term)
 constexpr uint32_t COORD_BYTES = SUB * 4;
 constexpr uint32_t STAGE_BYTES = 6 * COORD_BYTES;
 constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES;
@@ -149,13 +153,90 @@ BL_DEV void ff_warp_sum(float &hi, float &lo) {
   }
 }
 
-// Renormalise a float-float pair (TwoSum of hi and lo) so that lo is again
-// below half an ulp of hi; keeps the rounding of later lo updates small.
-BL_DEV void ff_renorm(float &hi, float &lo) {
-  const float s = __fadd_rn(hi, lo);
-  const float bp = __fsub_rn(s, hi);
-  lo = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(lo, bp));
-  hi = s;
+// Biased accumulation of the raw sums. Sum j keeps H = B_j + A, where A
+// is the sum of the terms added since the last fold and B_j a power-of-two
+// bias of at least twice the largest |A| possible, so that H stays in
+// [B/2, 3B/2]. B_j comes from per-coordinate power-of-two bounds S_a >= |z_a|
+// of the warp's particles: BIAS_MUL S_a for the coordinate sums and
+// BIAS_MUL S_a S_b for the products. Then s = H + term and s - H are exact
+// (Sterbenz' lemma), and the rounding error of s is the term minus (s - H):
+// exact for a coordinate (Fast2Sum), and for a product one more FMA that
+// rounds only that error (relative 2^-24 of it, at most 2^-48 B). The errors
+// go to the low part OL of the sum's float-float pair (OH, OL): four
+// instructions a term, against ten for TwoProd and TwoSum. Every FOLD_TERMS
+// terms at most, H - B (exact, again by Sterbenz) is added to the pair, which
+// is renormalised, and H restarts at B.
+BL_DEV void fb_add(float &H, float &OL, float x) {
+  const float s = __fadd_rn(H, x);
+  const float z = __fsub_rn(s, H);
+  OL = __fadd_rn(OL, __fsub_rn(x, z));
+  H = s;
+}
+
+BL_DEV void fb_add_prod(float &H, float &OL, float a, float b) {
+  const float s = __fmaf_rn(a, b, H);
+  const float z = __fsub_rn(s, H);
+  OL = __fadd_rn(OL, __fmaf_rn(a, b, -z));
+  H = s;
+}
+
+// Move H - B into the float-float pair (OH, OL) (TwoSum of OH and H - B),
+// renormalise the pair (Fast2Sum of OH and OL) and restart H at the bias B.
+BL_DEV void fb_fold(float &H, float B, float &OH, float &OL) {
+  const float d = __fsub_rn(H, B);
+  const float s = __fadd_rn(OH, d);
+  const float bp = __fsub_rn(s, OH);
+  const float e = __fadd_rn(__fsub_rn(OH, __fsub_rn(s, bp)), __fsub_rn(d, bp));
+  const float l = __fadd_rn(OL, e);
+  const float s2 = __fadd_rn(s, l);
+  OL = __fsub_rn(l, __fsub_rn(s2, s));
+  OH = s2;
+  H = B;
+}
+
+// Smallest power of two >= m (m finite, >= 0; 0 for 0), at most 2^127.
+BL_DEV float pow2_at_least(float m) {
+  const unsigned u = (__float_as_uint(m) + 0x007fffffu) & 0x7f800000u;
+  return __uint_as_float(min(u, 0x7f000000u));
+}
+
+// The bias of raw sum j (j < 6: coordinate j; then the products z_a z_b,
+// a <= b, row-major) from the coordinate bounds S.
+BL_DEV float fb_bias(int j, int a, int b, const float (&S)[6]) {
+  return j < 6 ? segk::BIAS_MUL * S[j] : segk::BIAS_MUL * S[a] * S[b];
+}
+
+// Fold sums J0 <= j < J1 into (OH, OL) and restart them at the biases of S.
+template <int J0, int J1>
+BL_DEV void fb_fold_subset(float (&H)[J1 - J0], float (&OH)[J1 - J0], float (&OL)[J1 - J0],
+                           const float (&S)[6]) {
+#pragma unroll
+  for (int a = 0; a < 6; ++a)
+    if (a >= J0 && a < J1) fb_fold(H[a - J0], fb_bias(a, 0, 0, S), OH[a - J0], OL[a - J0]);
+  int j = 6;
+#pragma unroll
+  for (int a = 0; a < 6; ++a)
+#pragma unroll
+    for (int b = a; b < 6; ++b) {
+      if (j >= J0 && j < J1) fb_fold(H[j - J0], fb_bias(j, a, b, S), OH[j - J0], OL[j - J0]);
+      ++j;
+    }
+}
+
+// Restart sums J0 <= j < J1 (already folded) at the biases of new bounds S.
+template <int J0, int J1>
+BL_DEV void fb_rebias_subset(float (&H)[J1 - J0], const float (&S)[6]) {
+#pragma unroll
+  for (int a = 0; a < 6; ++a)
+    if (a >= J0 && a < J1) H[a - J0] = fb_bias(a, 0, 0, S);
+  int j = 6;
+#pragma unroll
+  for (int a = 0; a < 6; ++a)
+#pragma unroll
+    for (int b = a; b < 6; ++b) {
+      if (j >= J0 && j < J1) H[j - J0] = fb_bias(j, a, b, S);
+      ++j;
+    }
 }
 
 // Issue the bulk copies of sub-chunk j (particles [q0, q0 + cnt)) into ring
@@ -173,20 +254,20 @@ BL_DEV void seg_issue(const Soa<float> &zin, int64_t q0, int64_t cnt, int s, uin
   }
 }
 
-// Float-float accumulation of the raw sums with index J0 <= j < J1 of one
-// particle: j < 6 the coordinates, then the 21 products z_a z_b (a <= b,
-// row-major).
+// Biased accumulation of the raw sums with index J0 <= j < J1 of one
+// particle (errors into the low parts L): j < 6 the coordinates, then the 21
+// products z_a z_b (a <= b, row-major).
 template <int J0, int J1>
-BL_DEV void mom_subset(float (&hi)[J1 - J0], float (&lo)[J1 - J0], const float (&v)[6]) {
+BL_DEV void mom_subset(float (&H)[J1 - J0], float (&L)[J1 - J0], const float (&v)[6]) {
 #pragma unroll
   for (int a = 0; a < 6; ++a)
-    if (a >= J0 && a < J1) ff_add(hi[a - J0], lo[a - J0], v[a]);
+    if (a >= J0 && a < J1) fb_add(H[a - J0], L[a - J0], v[a]);
   int j = 6;
 #pragma unroll
   for (int a = 0; a < 6; ++a)
 #pragma unroll
     for (int b = a; b < 6; ++b) {
-      if (j >= J0 && j < J1) ff_add_prod(hi[j - J0], lo[j - J0], v[a], v[b]);
+      if (j >= J0 && j < J1) fb_add_prod(H[j - J0], L[j - J0], v[a], v[b]);
       ++j;
     }
 }
@@ -201,22 +282,48 @@ BL_DEV float2 vec_make(const float (&o)[2]) { return make_float2(o[0], o[1]); }
 BL_DEV float4 vec_make(const float (&o)[4]) { return make_float4(o[0], o[1], o[2], o[3]); }
 
 // One group of PPT particles of one role: moments of the inputs (masked to
-// [lo, hi) when MASK) and the role's three output rows.
+// [lo, hi) when MASK) and the role's three output rows. When a particle of
+// the warp exceeds the bounds S of a coordinate the role uses (or is not
+// finite), the warp folds its sums, raises S to the next power of two of
+// the warp's largest finite |z_a| and restarts the sums at the new biases.
 template <int ROLE, bool APPLY, bool MOMENTS, bool MASK, bool HAS_C>
 BL_DEV void seg_group(const float (&v)[segk::PPT][6], int64_t p0, int64_t lo, int64_t hi,
                       const float (&M)[18], const float (&c)[6],
+                      float (&fH)[ROLE ? 13 : 14], float (&S)[6],
                       float (&shi)[ROLE ? 13 : 14], float (&slo)[ROLE ? 13 : 14], float &nf,
                       Soa<float> &zout) {
   constexpr int J0 = ROLE ? 14 : 0, J1 = ROLE ? 27 : 14;
+  constexpr int A0 = ROLE ? 1 : 0;  // first coordinate the role's sums use
   constexpr int P = segk::PPT;
   bool act[P];
 #pragma unroll
   for (int k = 0; k < P; ++k) act[k] = MASK ? (p0 + k >= lo && p0 + k < hi) : true;
   if (MOMENTS) {
+    bool out = false;
+#pragma unroll
+    for (int k = 0; k < P; ++k)
+#pragma unroll
+      for (int a = A0; a < 6; ++a) out |= act[k] && !(fabsf(v[k][a]) <= S[a]);
+    if (__any_sync(0xffffffffu, out)) {
+      fb_fold_subset<J0, J1>(fH, shi, slo, S);
+#pragma unroll
+      for (int a = A0; a < 6; ++a) {
+        float m = 0.0f;
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+          const float w = fabsf(v[k][a]);
+          if (act[k] && w <= 3.4028235e38f) m = fmaxf(m, w);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        S[a] = fmaxf(S[a], pow2_at_least(m));
+      }
+      fb_rebias_subset<J0, J1>(fH, S);
+    }
 #pragma unroll
     for (int k = 0; k < P; ++k) {
       if (!act[k]) continue;
-      mom_subset<J0, J1>(shi, slo, v[k]);
+      mom_subset<J0, J1>(fH, slo, v[k]);
       if (ROLE == 0) {
         // v * 0 is 0 for a finite value and NaN for an infinite or NaN one
         float t = 0.0f;
@@ -261,13 +368,20 @@ BL_DEV void seg_group(const float (&v)[segk::PPT][6], int64_t p0, int64_t lo, in
 }
 
 // Reduce the role's sums over the block's warps into one partial slot (28
-// doubles: sums 0..26 and the non-finite count) and clear them.
+// doubles: sums 0..26 and the non-finite count) and clear them; the bounds S
+// restart at 0 for the next bunch piece.
 template <int ROLE>
-BL_DEV void seg_flush(float (&shi)[ROLE ? 13 : 14], float (&slo)[ROLE ? 13 : 14], float &nf,
+BL_DEV void seg_flush(float (&fH)[ROLE ? 13 : 14], float (&S)[6], float (&shi)[ROLE ? 13 : 14],
+                      float (&slo)[ROLE ? 13 : 14], float &nf,
                       double (*red)[15], double *dst, int warp, int lane) {
   constexpr int NJ = ROLE ? 13 : 14;
+  constexpr int J0 = ROLE ? 14 : 0, J1 = ROLE ? 27 : 14;
+  fb_fold_subset<J0, J1>(fH, shi, slo, S);
+#pragma unroll
+  for (int a = 0; a < 6; ++a) S[a] = 0.0f;
 #pragma unroll
   for (int i = 0; i < NJ; ++i) {
+    fH[i] = 0.0f;
     ff_warp_sum(shi[i], slo[i]);
     if (lane == 0) red[warp][i] = (double)shi[i] + (double)slo[i];
     shi[i] = 0.0f;
@@ -337,10 +451,14 @@ BL_DEV void seg_consume(const Soa<float> &zin, Soa<float> &zout, int64_t n, int6
                         int warp, int lane) {
   using namespace segk;
   constexpr int NJ = ROLE ? 13 : 14;
-  const int g = (warp >> 1) * 32 + lane;  // particle group 0..127 of a stage (PPT particles)
-  float shi[NJ], slo[NJ], nf = 0.0f;
+  const int g = (warp >> 1) * 32 + lane;  // particle group of a pass (PPT particles)
+  // biased sums fH with their coordinate bounds S, and the float-float pairs
+  // (shi, slo) they are folded into; S = 0 gives the biases 0 = fH
+  float fH[NJ], S[6], shi[NJ], slo[NJ], nf = 0.0f;
 #pragma unroll
-  for (int i = 0; i < NJ; ++i) { shi[i] = 0.0f; slo[i] = 0.0f; }
+  for (int i = 0; i < NJ; ++i) { fH[i] = 0.0f; shi[i] = 0.0f; slo[i] = 0.0f; }
+#pragma unroll
+  for (int a = 0; a < 6; ++a) S[a] = 0.0f;
   float M[18], c[6];
   int b = find_bunch(offsets, n_bunch, r_lo);
   int64_t pe = bunch_end(offsets, b, n);
@@ -370,12 +488,13 @@ BL_DEV void seg_consume(const Soa<float> &zin, Soa<float> &zout, int64_t n, int6
         if (it == PASSES - 1) seg_release(s, j, nsub, r_hi, r_lo, zin, sb, full0, empty0, s_cnt,
                                           s_issued, err, lane);
         seg_group<ROLE, APPLY, MOMENTS, false, HAS_C>(v, q0 + it * PASS + PPT * g, 0, 0, M, c,
-                                                      shi, slo, nf, zout);
+                                                      fH, S, shi, slo, nf, zout);
       }
       open = true;
       if (pe == q1) {  // bunch b ends with this stage
         if (MOMENTS) {
-          seg_flush<ROLE>(shi, slo, nf, red, partials + ((int64_t)b + blockIdx.x) * 28, warp, lane);
+          seg_flush<ROLE>(fH, S, shi, slo, nf, red,
+                          partials + ((int64_t)b + blockIdx.x) * 28, warp, lane);
           open = false;
         }
         if (b + 1 < n_bunch) {
@@ -418,13 +537,14 @@ BL_DEV void seg_consume(const Soa<float> &zin, Soa<float> &zout, int64_t n, int6
         for (;;) {
           const int64_t hi = min(a1, pe);
           if (hi > cur) {
-            seg_group<ROLE, APPLY, MOMENTS, true, HAS_C>(v, p0, cur, hi, M, c, shi, slo, nf, zout);
+            seg_group<ROLE, APPLY, MOMENTS, true, HAS_C>(v, p0, cur, hi, M, c, fH, S, shi, slo,
+                                                         nf, zout);
             open = true;
           }
           if (hi < pe) break;  // bunch b goes on past this pass
           if (MOMENTS && open) {
-            seg_flush<ROLE>(shi, slo, nf, red, partials + ((int64_t)b + blockIdx.x) * 28, warp,
-                            lane);
+            seg_flush<ROLE>(fH, S, shi, slo, nf, red,
+                            partials + ((int64_t)b + blockIdx.x) * 28, warp, lane);
             open = false;
           }
           if (++b >= n_bunch) break;
@@ -437,17 +557,16 @@ BL_DEV void seg_consume(const Soa<float> &zin, Soa<float> &zout, int64_t n, int6
       }
       seg_release(s, j, nsub, r_hi, r_lo, zin, sb, full0, empty0, s_cnt, s_issued, err, lane);
     }
-    if (MOMENTS && (j % RENORM_SUBS) == RENORM_SUBS - 1) {
-#pragma unroll
-      for (int i = 0; i < NJ; ++i) ff_renorm(shi[i], slo[i]);
-    }
+    if (MOMENTS && (j % FOLD_SUBS) == FOLD_SUBS - 1)
+      fb_fold_subset<ROLE ? 14 : 0, ROLE ? 27 : 14>(fH, shi, slo, S);
   }
   if (MOMENTS && open)
-    seg_flush<ROLE>(shi, slo, nf, red, partials + ((int64_t)b + blockIdx.x) * 28, warp, lane);
+    seg_flush<ROLE>(fH, S, shi, slo, nf, red, partials + ((int64_t)b + blockIdx.x) * 28,
+                    warp, lane);
 }
 
 template <bool APPLY, bool MOMENTS, bool HAS_C>
-__global__ void __launch_bounds__(segk::THREADS, 2)
+__global__ void __launch_bounds__(segk::THREADS, 1)
 seg_f32_kernel(Soa<float> zin, Soa<float> zout, int64_t n, int64_t per_cta,
                const int64_t *__restrict__ offsets, int n_bunch, const float *__restrict__ mats,
                int per_bunch, const float *__restrict__ centers, double *__restrict__ partials,
@@ -499,11 +618,11 @@ seg_f32_kernel(Soa<float> zin, Soa<float> zout, int64_t n, int64_t per_cta,
   }
 }
 
-// Sub-chunks per CTA for n particles: the range of 2 CTAs per SM, at least
+// Sub-chunks per CTA for n particles: the range of one CTA per SM, at least
 // MIN_SUB_PER_CTA.
 int64_t seg_per_cta(int64_t n, int num_sms) {
   const int64_t S = (n + segk::SUB - 1) / segk::SUB;
-  const int64_t G = 2 * (int64_t)std::max(num_sms, 1);
+  const int64_t G = (int64_t)std::max(num_sms, 1);
   return std::max<int64_t>(segk::MIN_SUB_PER_CTA, (S + G - 1) / G);
 }
 

@@ -41,7 +41,8 @@ def _cmp_moments(got, want, tol):
     return err
 
 
-@pytest.mark.parametrize("n", [1, 2, 127, 128, 129, 4095, 4096, 4097, 10000, (1 << 18) + 3])
+@pytest.mark.parametrize("n", [1, 2, 127, 128, 129, 2047, 2048, 2049, 4095, 4096, 4097, 8191,
+                               8192, 8193, 10000, (1 << 18) + 3])
 def test_moments_fp32(n):
     from paper_2402_17248_gb300 import bl
     z, g = _bunch(n, seed=n)
@@ -78,6 +79,43 @@ def test_moments_many_bunches_with_empty_and_tiny():
             _cmp_moments(got[i], want, 1e-10)
         else:
             assert got[i][0] == c
+
+
+def test_moments_growing_scale_and_outliers():
+    """The FP32 sums keep per-coordinate power-of-two bounds that start at
+    zero and are raised when a larger particle arrives: particles whose size
+    grows 1e4-fold along the array, with outliers at ~1000 sigma and a
+    centroid offset, still match the oracle."""
+    from paper_2402_17248_gb300 import bl
+    n = 300007
+    z, g = _bunch(n, seed=21)
+    rng = np.random.default_rng(21)
+    grow = np.geomspace(1e-4, 1.0, n)
+    z = [a * grow for a in z]
+    for a in z:
+        idx = rng.choice(n, 7, replace=False)
+        a[idx] *= 1e3 * rng.choice([-1.0, 1.0], 7)
+    z[1] = z[1] + 3.0 * z[1].std()
+    z32 = as_f32(z)
+    _cmp_moments(bl.bl_moments(to_bunch(z32, g))[0], moments.moments28(z32), 1e-10)
+
+
+def test_moments_bunches_of_very_different_size():
+    """Bounds restart at every bunch: a bunch 1e6 times smaller than the one
+    before it is summed at its own scale."""
+    from paper_2402_17248_gb300 import bl
+    counts = [40000, 9000, 40000, 3, 20000]
+    scale = [1.0, 1e-6, 1e3, 1.0, 1e-3]
+    off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    z, g = _bunch(int(off[-1]), seed=33)
+    for i in range(len(counts)):
+        for a in z:
+            a[off[i]:off[i + 1]] *= scale[i]
+    z32 = as_f32(z)
+    got = bl.bl_moments(to_bunch(z32, g, offsets=off))
+    for i in range(len(counts)):
+        want = moments.moments28([a[off[i]:off[i + 1]] for a in z32])
+        _cmp_moments(got[i], want, 1e-10)
 
 
 def _segment(bg, k=lattice.DESIGN_K):
