@@ -203,8 +203,10 @@ bl_status bl_track_expand_moments(const bl_lattice *lat, int32_t n_bunch,
 
 /* Per-bunch moments of the current particles (Sec. 4 moments, definitions as
  * in bl_track). out: host or device, n_bunch * 28 doubles; valid after the
- * stream is synchronised. Accumulation: exact FP32 products and float-float
- * sums per thread, FP64 across threads. Uses library scratch memory. */
+ * stream is synchronised. Accumulation (FP32 bunches): per thread, biased
+ * FP32 sums whose rounding errors (products included) are recovered exactly
+ * and folded into float-float pairs; FP64 across threads. FP64 bunches: FP64
+ * sums. Uses library scratch memory. */
 bl_status bl_moments(const bl_bunch *bunch, double *out, bl_stream stream);
 
 /* Size of the fixed scratch used by bl_moments_noalloc, in partial-sum
