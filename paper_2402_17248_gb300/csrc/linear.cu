@@ -822,13 +822,116 @@ linear_adjoint_kernel(Soa<T> lam, Soa<T> zin, int64_t n, const int64_t *__restri
   }
 }
 
+// FP32 form: each thread loads AP particles (strided by the block size, so
+// every load is coalesced) before it uses any, keeping 48 loads in flight;
+// the 36 float-float sums are reduced across the block through shared
+// memory in four rounds of 9 (float-float within a round, FP64 only for the
+// last 28 partials of a sum), instead of FP64 warp shuffles.
+namespace adjk {
+constexpr int AP = 4;                 // particles per thread and iteration
+constexpr int RS = 9;                 // sums per reduction round
+constexpr int PARTS = STREAM_THREADS / RS;  // 28 partials per sum in a round
+}  // namespace adjk
+
+__global__ void __launch_bounds__(STREAM_THREADS, 1)
+linear_adjoint_f32_kernel(Soa<float> lam, Soa<float> zin, int64_t n,
+                          const int64_t *__restrict__ offsets, int n_bunch,
+                          const float *__restrict__ mats, int per_bunch,
+                          double *__restrict__ partials) {
+  using namespace adjk;
+  __shared__ int s_b0;
+  __shared__ float s_h[RS][STREAM_THREADS], s_l[RS][STREAM_THREADS];
+  __shared__ float s_ph[RS][PARTS], s_pl[RS][PARTS];
+  __shared__ double s_res[36];
+  const int tid = threadIdx.x;
+  const int64_t start = (int64_t)blockIdx.x * STREAM_CHUNK;
+  const int64_t end = min(n, start + STREAM_CHUNK);
+  if (tid == 0) s_b0 = find_bunch(offsets, n_bunch, start);
+  __syncthreads();
+  int b = s_b0;
+  int64_t lo = start;
+  while (lo < end) {
+    const int64_t hi = min(end, bunch_end(offsets, b, n));
+    if (hi > lo) {
+      float M[36];
+      const float *Mb = mats + (per_bunch ? (int64_t)b * 36 : 0);
+#pragma unroll
+      for (int i = 0; i < 36; ++i) M[i] = __ldg(Mb + i);
+      float chi[36], clo[36];
+#pragma unroll
+      for (int i = 0; i < 36; ++i) { chi[i] = 0.f; clo[i] = 0.f; }
+      for (int64_t p0 = lo + tid; p0 < hi; p0 += (int64_t)AP * STREAM_THREADS) {
+        float l[AP][6], z[AP][6];
+#pragma unroll
+        for (int k = 0; k < AP; ++k) {
+          const int64_t p = p0 + (int64_t)k * STREAM_THREADS;
+#pragma unroll
+          for (int i = 0; i < 6; ++i) {
+            l[k][i] = p < hi ? lam.c[i][p] : 0.f;
+            z[k][i] = p < hi ? zin.c[i][p] : 0.f;
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < AP; ++k) {
+          const int64_t p = p0 + (int64_t)k * STREAM_THREADS;
+          if (p >= hi) break;
+#pragma unroll
+          for (int a = 0; a < 6; ++a)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) ff_add_prod(chi[a * 6 + c], clo[a * 6 + c], l[k][a], z[k][c]);
+#pragma unroll
+          for (int j = 0; j < 6; ++j) {
+            float s = 0.f;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) s = fmaf(M[i * 6 + j], l[k][i], s);
+            lam.c[j][p] = s;
+          }
+        }
+      }
+      // block reduction of the 36 sums, RS at a time
+#pragma unroll
+      for (int r = 0; r < 36 / RS; ++r) {
+#pragma unroll
+        for (int i = 0; i < RS; ++i) { s_h[i][tid] = chi[r * RS + i]; s_l[i][tid] = clo[r * RS + i]; }
+        __syncthreads();
+        if (tid < RS * PARTS) {
+          const int j = tid / PARTS, q = tid - j * PARTS;
+          float h = 0.f, l2 = 0.f;
+          for (int t = q; t < STREAM_THREADS; t += PARTS) {
+            ff_add(h, l2, s_h[j][t]);
+            l2 = __fadd_rn(l2, s_l[j][t]);
+          }
+          s_ph[j][q] = h;
+          s_pl[j][q] = l2;
+        }
+        __syncthreads();
+        if (tid < RS) {
+          double acc = 0.0;
+          for (int q = 0; q < PARTS; ++q) acc += (double)s_ph[tid][q] + (double)s_pl[tid][q];
+          s_res[r * RS + tid] = acc;
+        }
+        __syncthreads();
+      }
+      if (tid < 36) partials[((int64_t)b + blockIdx.x) * 36 + tid] = s_res[tid];
+      __syncthreads();
+    }
+    lo = max(lo, hi);
+    ++b;
+    if (b >= n_bunch) break;
+  }
+}
+
 template <typename T>
 cudaError_t launch_linear_adjoint(Soa<T> lam, Soa<T> zin, int64_t n, const int64_t *offsets,
                                   int n_bunch, const T *mats, int per_bunch, double *partials,
                                   cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  linear_adjoint_kernel<T><<<(unsigned)stream_blocks(n), STREAM_THREADS, 0, st>>>(
-      lam, zin, n, offsets, n_bunch, mats, per_bunch, partials);
+  if constexpr (sizeof(T) == 4)
+    linear_adjoint_f32_kernel<<<(unsigned)stream_blocks(n), STREAM_THREADS, 0, st>>>(
+        lam, zin, n, offsets, n_bunch, mats, per_bunch, partials);
+  else
+    linear_adjoint_kernel<T><<<(unsigned)stream_blocks(n), STREAM_THREADS, 0, st>>>(
+        lam, zin, n, offsets, n_bunch, mats, per_bunch, partials);
   return cudaGetLastError();
 }
 template cudaError_t launch_linear_adjoint<float>(Soa<float>, Soa<float>, int64_t, const int64_t *,
